@@ -1,0 +1,427 @@
+"""Throughput benchmark of the resampling F-statistic on one GB300 (or N replicas).
+
+Workload: the narrowband single-target search (H1 + L1, 10 days at dt = 0.5 s,
+1 728 000 complex64 samples per detector, FFT 2^22, one sky position,
+8192 f1dot x 4 f2dot = 32 768 templates), seeded Gaussian noise.  One step is
+the whole hot path over that job: per-sky work (Sec. 3 steps iii-v) plus
+steps vi-vii for all 32 768 templates, 2F written for every bin.
+
+Printed JSON line: templates/s (value), 2F-bins/s, the dominant kernel's
+HBM roofline, the FP64-GPU comparison path, the oracle on the host cores,
+end-to-end through host buffers, and clocks sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import config2, make_noise  # noqa: E402
+
+METRIC = "templates/s and 2F-bins/s on 1 GB300 at |d2F|<=1e-3·2F+0.02 vs plain FP64-GPU path"
+UNIT = "templates/s"
+WORKLOAD = ("narrowband single target: H1+L1, 10 d, dt=0.5 s, 1,728,000 c64 samples/det, "
+            "FFT 2^22, 1 sky x 8192 f1dot x 4 f2dot = 32,768 templates, Dterms 8")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--templates", type=int, default=0, help="templates per step (0 = full job)")
+    ap.add_argument("--chunk", type=int, default=256, help="templates per fstat_compute call")
+    ap.add_argument("--fp64-templates", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in self.rows if num(r[0])]
+        mx = [num(r[1]) for r in self.rows if num(r[1])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower().startswith("active")})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("fft_impl.cuh", "fstat_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2201_00451_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t[kernel]
+        if e.get("source_hash") == kernel_source_hash():
+            return float(e["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def make_inputs(t, rank):
+    return [make_noise(t.seed + 7919 * rank, X, t.n_samples, t.sigmas[X], "c64")
+            for X in range(len(t.detectors))]
+
+
+# ------------------------------------------------------------- CPU oracle
+def cpu_oracle_timing(t, xs, n_tmpl_total, n_sample_tmpl=2):
+    """The FP64 oracle as it stands on a bounded sample: one per-sky step
+    (iii-v) and ``n_sample_tmpl`` templates of steps vi-vii, extrapolated to
+    the full job."""
+    from oracle import resamp
+
+    a, d = t.skies[0]
+    t0 = time.perf_counter()
+    prep = resamp.sky_prep(t, xs, a, d)
+    t_sky = time.perf_counter() - t0
+    tm = t.templates()
+    times = []
+    for k in range(n_sample_tmpl):
+        s = time.perf_counter()
+        resamp.twoF(t, prep, float(tm["f1dot"][k]), float(tm["f2dot"][k]))
+        times.append(time.perf_counter() - s)
+    t_tmpl = sum(times) / len(times)
+    value = n_tmpl_total / (t_sky + n_tmpl_total * t_tmpl)
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 per-sky step (2 det x {t.n_samples} samples) in {t_sky:.2f} s + "
+                      f"{n_sample_tmpl} templates of 2 x 2^{int(math.log2(t.n_fft))} FFTs at "
+                      f"{t_tmpl:.2f} s each, extrapolated to {n_tmpl_total} templates"}, t_sky, t_tmpl
+
+
+# ------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    t = config2()
+    xs = make_inputs(t, 0)
+    from oracle import resamp
+
+    a, d = t.skies[0]
+    s = time.perf_counter()
+    prep = resamp.sky_prep(t, xs, a, d)
+    t_sky = time.perf_counter() - s
+    tm = t.templates()
+    for k in range(args.warmup):
+        resamp.twoF(t, prep, float(tm["f1dot"][k]), float(tm["f2dot"][k]))
+    times = []
+    for k in range(args.steps):
+        s = time.perf_counter()
+        resamp.twoF(t, prep, float(tm["f1dot"][k]), float(tm["f2dot"][k]))
+        times.append(time.perf_counter() - s)
+    n = t.n_templates
+    t_tmpl = sum(times) / len(times)
+    value = n / (t_sky + n * t_tmpl)
+    sample = (f"per-sky step once ({t_sky:.2f} s) + one template per step ({t_tmpl:.2f} s), "
+              f"extrapolated to {n} templates")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": (t_sky + n * t_tmpl) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+    from paper_2201_00451_gb300 import build as fbuild
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        fbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    pkg.load()
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    t = config2()
+    xs = make_inputs(t, rank)
+    tm_all = pkg.as_templates(t.templates())
+    n_tmpl = args.templates or len(tm_all)
+    tm = tm_all[:n_tmpl] if n_tmpl <= len(tm_all) else np.resize(tm_all, n_tmpl)
+    chunk = min(args.chunk, n_tmpl)
+    n_fft = t.n_fft
+
+    plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
+    for X in range(len(t.detectors)):
+        plan.set_data(X, xs[X], t.sigmas[X])
+    out = torch.empty((chunk, n_fft), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > L2
+    chunks = [tm[i:i + chunk] for i in range(0, n_tmpl, chunk)]
+
+    def step():
+        plan.invalidate_sky()
+        for c in chunks:
+            plan.compute_ptr(c, out.data_ptr(), stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    plan.sync()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    plan.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()                      # untimed: evict L2 between steps
+        barrier()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        barrier()
+    plan.sync()
+    clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    stats = {k: plan.kernel_stats(k) for k in (0, 1, 2)}
+    plan.set_profiling(False)
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    total_tmpl = n_tmpl * args.steps * world
+    value = total_tmpl / (ms / 1e3)
+    launches = args.steps * (len(chunks) + 2 * n_tmpl + 3 + len(t.detectors))
+
+    # dominant kernel roofline (algorithmic bytes: 16 B per sample read for
+    # pass A, 4 B per bin written for pass B)
+    peak, peak_kind = peaks()
+    n1, n2 = plan.split
+    kinfo = {0: ("pass_a", 16.0 * t.n_samples), 1: ("pass_b", 4.0 * n_fft)}
+    dom = max((0, 1), key=lambda k: stats[k][1])
+    nl, tot = stats[dom]
+    avg_s = tot / 1e3 / max(nl, 1)
+    name, bytes_alg = kinfo[dom]
+    achieved = bytes_alg / avg_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": ncu_traffic(name), "kernel": name,
+            "peak_source": peak_kind,
+            "kernels_ms_per_launch": {kinfo[k][0]: stats[k][1] / max(stats[k][0], 1) for k in (0, 1)},
+            "per_sky_ms": stats[2][1] / max(stats[2][0], 1),
+            "path": {"bytes_per_template": 16.0 * t.n_samples + 4.0 * n_fft,
+                     "achieved_GBps": (16.0 * t.n_samples + 4.0 * n_fft) * value / world / 1e9,
+                     "frac": (16.0 * t.n_samples + 4.0 * n_fft) * value / world / 1e9 / peak},
+            "split": [n1, n2]}
+    plan.close()
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "bins_per_s": value * n_fft,
+                "tau_F_eff_s": 1.0 / (value * n_fft * len(t.detectors)),
+                "config": {"workload": WORKLOAD, "templates_per_step": n_tmpl, "chunk": chunk,
+                           "precision": "mixed: FP64 timing and phases, FP32 resample/FFT/2F",
+                           "l2": "flushed between steps (256 MB write, untimed)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "gpu_launches": launches, "clocks": clocks.summary()}
+
+    # FP64-GPU comparison path (same kernels in FP64), timed on a subset
+    if rank == 0 and not args.no_fp64:
+        line["fp64_gpu"] = fp64_gpu(t, xs, tm_all, args.fp64_templates, dev, stream, value)
+
+    # end-to-end: host x_h (pinned) -> device, compute, 2F back to pinned host
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e(t, xs, tm, chunk, dev, stream, args)
+
+    if rank == 0 and not args.no_cpu:
+        cb, _, _ = cpu_oracle_timing(t, [x.astype(np.complex128) for x in xs], len(tm_all))
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def fp64_gpu(t, xs, tm_all, n, dev, stream, mixed_value):
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+
+    plan = pkg.FstatPlan.from_target(t, pkg.FP64)
+    for X in range(len(t.detectors)):
+        plan.set_data(X, xs[X], t.sigmas[X])
+    out = torch.empty((n, t.n_fft), dtype=torch.float32, device=dev)
+    sub = tm_all[:n]
+    plan.compute_ptr(sub[:1], out.data_ptr(), stream)   # warm-up
+    plan.sync()
+    plan.set_profiling(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.invalidate_sky()
+    a.record(stream)
+    plan.compute_ptr(sub, out.data_ptr(), stream)
+    b.record(stream)
+    plan.sync()
+    ms = a.elapsed_time(b)
+    n_sky, ms_sky = plan.kernel_stats(2)
+    plan.close()
+    per_t = (ms - ms_sky) / n
+    total = t.n_templates
+    v = total / ((ms_sky + total * per_t) / 1e3)
+    return {"value": v, "unit": UNIT, "sample": f"per-sky step + {n} templates, extrapolated to {total}",
+            "mixed_over_fp64": mixed_value / v}
+
+
+def e2e(t, xs, tm, chunk, dev, stream, args):
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+
+    n_fft = t.n_fft
+    hx = [torch.from_numpy(x).pin_memory() for x in xs]
+    plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
+    dbuf = [torch.empty((chunk, n_fft), dtype=torch.float32, device=dev) for _ in range(2)]
+    hbuf = [torch.empty((chunk, n_fft), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    copy = torch.cuda.Stream(dev)
+    done = [torch.cuda.Event() for _ in range(2)]
+    chunks = [tm[i:i + chunk] for i in range(0, len(tm), chunk)]
+
+    def step():
+        for X in range(len(t.detectors)):
+            plan.set_data(X, hx[X].numpy(), t.sigmas[X])   # pinned host -> device
+        for i, c in enumerate(chunks):
+            k = i & 1
+            stream.wait_event(done[k])       # device buffer k free again
+            plan.compute_ptr(c, dbuf[k].data_ptr(), stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            copy.wait_event(ev)
+            with torch.cuda.stream(copy):
+                hbuf[k][: len(c)].copy_(dbuf[k][: len(c)], non_blocking=True)
+            done[k].record(copy)
+        copy.synchronize()
+        stream.synchronize()
+
+    for _ in range(1):
+        step()
+    torch.cuda.synchronize(dev)
+    s = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - s
+    plan.close()
+    n = len(tm) * args.steps
+    return {"value": n / el, "unit": UNIT,
+            "h2d_bytes_per_step": int(sum(x.nbytes for x in xs)),
+            "d2h_bytes_per_step": int(len(tm) * n_fft * 4)}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * fstat.h -- C ABI of the GB300 resampling F-statistic library (libfstat.so).
+ *
+ * The library computes the coherent F-statistic of continuous-gravitational-
+ * wave searches by the resampling ("Resamp") method of Dunn, Clearwater,
+ * Melatos & Wette, arXiv:2201.00451, Sec. 3 steps (iii)-(vii), for every
+ * frequency bin of a band centred on a heterodyne frequency f_h:
+ *
+ *   (iii) z_X(t_k) = x_h,X(t_k) exp(-i 2 pi f_h t_m,X(t_k))      (Sec. 3)
+ *   (iv)  regular SSB epochs t_b^j, detector epochs T_X^j          (Sec. 3)
+ *   (v)   z_X(T_X^j) by a Dterms Dirichlet-kernel interpolator     (Sec. 3)
+ *   (vi)  Fa, Fb = FFT of w a z e^{-i Phi_s}, w b z e^{-i Phi_s}    (eqs. Fa, Fb)
+ *   (vii) 2F = 2 (B|Fa|^2 + A|Fb|^2 - 2C Re(Fa Fb*)) / D          (eq. Fstat)
+ *
+ * All per-template work runs in hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions for every entry point:
+ *  - Return value: FSTAT_OK (0) or a negative FSTAT_ERR_* code.  No C++
+ *    exception crosses the ABI.  fstat_strerror() names a code.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued asynchronously on it unless stated.
+ *  - Errors found inside kernels (degenerate antenna matrix, non-finite
+ *    input) are recorded in the plan and returned by fstat_sync() and by
+ *    the next call that synchronises.
+ *  - A plan is not thread-safe; distinct plans may be used concurrently.
+ *  - Times are seconds, angles radians, frequencies Hz.
+ */
+#ifndef FSTAT_H
+#define FSTAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSTAT_MAX_DET 4
+
+enum {
+  FSTAT_OK = 0,
+  FSTAT_ERR_INVALID_ARG = -1, /* bad pointer, size, or out-of-range field     */
+  FSTAT_ERR_OOM = -2,         /* a device or pinned host allocation failed    */
+  FSTAT_ERR_CUDA = -3,        /* a CUDA runtime call or kernel launch failed  */
+  FSTAT_ERR_DEGENERATE = -4,  /* D = AB - C^2 <= 1e-12 AB for a sky position  */
+  FSTAT_ERR_NONFINITE = -5,   /* NaN or Inf in the input series               */
+  FSTAT_ERR_NOT_READY = -6,   /* compute before every detector has data       */
+  FSTAT_ERR_UNSUPPORTED = -7  /* size outside the compiled FFT range          */
+};
+
+enum { FSTAT_MIXED = 0, /* FP64 timing/phases, FP32 resample/FFT/2F        */
+       FSTAT_FP64 = 1   /* every step in FP64 (comparison path)           */ };
+
+enum { FSTAT_C64 = 0,  /* interleaved float  (re, im) */
+       FSTAT_C128 = 1  /* interleaved double (re, im) */ };
+
+/* Interferometer site: geodetic latitude, longitude (east positive) and the
+ * angle gamma of the arm bisector, counter-clockwise from local East.  The
+ * antenna patterns a(t), b(t) are those of Jaranowski, Krolak & Schutz (1998)
+ * eqs. (12)-(13), which the paper cites in Sec. 2. */
+typedef struct {
+  double lat_rad, lon_rad, gamma_rad;
+} fstat_detector;
+
+/* Simplified ephemeris for the Roemer delay t_m of Sec. 2 (phase model):
+ *   r_orb = au (cos th, cos(obl) sin th, sin(obl) sin th), th = orb_phase0 + omega_orb t
+ *   r_rot = r_earth (cos lat cos ph, cos lat sin ph, sin lat), ph = lon + sidereal_phase0 + omega_rot t
+ *   t_m   = (r_orb + r_rot) . n(alpha, delta) / c                                          */
+typedef struct {
+  double c, au, r_earth, omega_rot, omega_orb, obliquity, orb_phase0, sidereal_phase0;
+} fstat_ephemeris;
+
+/* Plan description.  All detectors share the sample grid t_k = t0 + k dt,
+ * k = 0..n_samples-1.  The SSB grid for a sky position is
+ * t_b^j = t_b^0 + j dt with t_b^0 = t0 + (orbital Roemer delay at the data
+ * midpoint t0 + n_samples dt / 2).  Output bins: 2F[m] at
+ * f_m = f_het + (m - n_fft/2) / (n_fft dt), m = 0..n_fft-1 (ascending).   */
+typedef struct {
+  int32_t n_det;      /* 1..FSTAT_MAX_DET                                    */
+  int32_t dterms;     /* interpolation half-width D (taps k0-D..k0+D), 1..32 */
+  int32_t precision;  /* FSTAT_MIXED or FSTAT_FP64                           */
+  int32_t reserved;   /* must be 0                                           */
+  fstat_detector det[FSTAT_MAX_DET];
+  double t0, dt;      /* first sample time, sample spacing (> 0)            */
+  int64_t n_samples;  /* N, 1..2^24-1                                        */
+  double f_het;       /* heterodyne frequency f_h                            */
+  int64_t n_fft;      /* zero-padded FFT length: power of two, 2^10..2^24, >= N */
+  double t_ref;       /* spindown reference time; NaN -> t0 + floor(N/2) dt  */
+  fstat_ephemeris ephem;
+} fstat_plan_desc;
+
+/* One template: sky position and spindowns (Phi_s = 2 pi (f1dot tau^2/2 +
+ * f2dot tau^3/6), tau = t_b - t_ref; Sec. 2 phase model). */
+typedef struct {
+  double alpha, delta, f1dot, f2dot;
+} fstat_template;
+
+typedef struct fstat_plan fstat_plan;
+
+/* Create a plan on the current CUDA device.  Allocates all device buffers
+ * the plan needs (x_h copies, per-sky resampled series, FFT workspace).
+ * *out receives the plan; destroy it with fstat_plan_destroy.
+ * Errors: INVALID_ARG (NULL pointers, fields out of range), UNSUPPORTED
+ * (n_fft outside 2^10..2^24), OOM, CUDA. */
+int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out);
+
+/* Copy detector `det`'s heterodyned, downsampled series x_h (the output of
+ * Sec. 3 step ii) into the plan.  `xh` is a host or device pointer to n
+ * complex samples of type `dtype` (FSTAT_C64/FSTAT_C128); the caller keeps
+ * ownership.  `sigma` is the per-quadrature noise standard deviation of
+ * this detector; the noise weight is w = 1/(2 sigma^2).  Synchronises
+ * `stream` to validate the data.  Errors: INVALID_ARG (n != n_samples,
+ * sigma <= 0, det out of range), NONFINITE (NaN/Inf in xh), CUDA. */
+int fstat_set_data(fstat_plan* plan, int det, const void* xh, int dtype, int64_t n,
+                   double sigma, void* stream);
+
+/* 2F for n_tmpl templates.  `tmpl` is a HOST array of n_tmpl templates;
+ * `twoF` is a caller-owned DEVICE buffer of n_tmpl * n_fft floats, written
+ * row-major [template][bin] in ascending frequency.  Templates are grouped
+ * by sky position internally; per-sky work (steps iii-v) runs once per group
+ * and is reused across calls while the sky position does not change.
+ * Errors: INVALID_ARG, NOT_READY (a detector has no data), CUDA; kernel-side
+ * DEGENERATE is reported by fstat_sync. */
+int fstat_compute(fstat_plan* plan, const fstat_template* tmpl, int64_t n_tmpl, float* twoF,
+                  void* stream);
+
+/* Frequency axis of the output: f_m = *f0 + m * *df. */
+int fstat_freq_axis(const fstat_plan* plan, double* f0, double* df);
+
+/* Forget the cached per-sky work so the next fstat_compute redoes it. */
+int fstat_invalidate_sky(fstat_plan* plan);
+
+/* Run the per-sky steps (iii)-(v) for (alpha, delta) and copy the detector-
+ * summed, antenna-weighted resampled series to the host: ga, gb receive
+ * n_samples complex doubles each (interleaved re, im; NULL to skip) and
+ * abcd receives A, B, C, D (NULL to skip).  Synchronises `stream`. */
+int fstat_export_sky(fstat_plan* plan, double alpha, double delta, double* ga, double* gb,
+                     double* abcd, void* stream);
+
+/* Wait for all work the plan enqueued and return the first recorded error. */
+int fstat_sync(fstat_plan* plan);
+
+/* Per-kernel timing with CUDA events recorded around each launch on the
+ * launching stream (off by default).  kernel: 0 = FFT pass A (spindown
+ * phase + column FFTs), 1 = FFT pass B (row FFTs + 2F), 2 = per-sky work.
+ * fstat_kernel_stats synchronises and returns the launch count and the
+ * summed event time since profiling was enabled. */
+int fstat_set_profiling(fstat_plan* plan, int enable);
+int fstat_kernel_stats(fstat_plan* plan, int kernel, int64_t* launches, double* total_ms);
+
+/* FFT split chosen for this plan: n_fft = n1 * n2 (pass A length n2, pass B
+ * length n1).  fstat_set_split overrides it (both powers of two in
+ * 32..4096); the autotuner uses it. */
+int fstat_get_split(const fstat_plan* plan, int64_t* n1, int64_t* n2);
+int fstat_set_split(fstat_plan* plan, int64_t n1);
+
+void fstat_plan_destroy(fstat_plan* plan);
+const char* fstat_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSTAT_H */

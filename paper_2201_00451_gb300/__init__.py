@@ -1,0 +1,291 @@
+"""Python binding of libfstat (GB300 resampling F-statistic).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libfstat.so``.  PyTorch is used for device memory (output
+tensors) and stream handles.  The names follow the C ABI in
+``include/fstat.h``.
+
+The library is built in-tree by ``paper_2201_00451_gb300.build.build()``.
+Importing this package does not load it; the first use does, and raises
+``FstatLibraryMissing`` if the shared library has not been built -- there
+is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfstat.so")
+
+MAX_DET = 4
+OK = 0
+ERR = {
+    -1: "FSTAT_ERR_INVALID_ARG",
+    -2: "FSTAT_ERR_OOM",
+    -3: "FSTAT_ERR_CUDA",
+    -4: "FSTAT_ERR_DEGENERATE",
+    -5: "FSTAT_ERR_NONFINITE",
+    -6: "FSTAT_ERR_NOT_READY",
+    -7: "FSTAT_ERR_UNSUPPORTED",
+}
+MIXED, FP64 = 0, 1
+C64, C128 = 0, 1
+
+# Every symbol include/fstat.h declares (checked by the tests).
+EXPORTS = (
+    "fstat_plan_create", "fstat_set_data", "fstat_compute", "fstat_freq_axis",
+    "fstat_invalidate_sky", "fstat_export_sky", "fstat_sync", "fstat_set_profiling",
+    "fstat_kernel_stats", "fstat_get_split", "fstat_set_split", "fstat_plan_destroy",
+    "fstat_strerror",
+)
+
+
+class FstatLibraryMissing(ImportError):
+    pass
+
+
+class FstatError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERR.get(code, code)} ({_strerror(code)})")
+
+
+class Detector(ctypes.Structure):
+    _fields_ = [("lat_rad", ctypes.c_double), ("lon_rad", ctypes.c_double),
+                ("gamma_rad", ctypes.c_double)]
+
+
+class Ephemeris(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in (
+        "c", "au", "r_earth", "omega_rot", "omega_orb", "obliquity", "orb_phase0", "sidereal_phase0")]
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_det", ctypes.c_int32), ("dterms", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("det", Detector * MAX_DET), ("t0", ctypes.c_double),
+        ("dt", ctypes.c_double), ("n_samples", ctypes.c_int64), ("f_het", ctypes.c_double),
+        ("n_fft", ctypes.c_int64), ("t_ref", ctypes.c_double), ("ephem", Ephemeris),
+    ]
+
+
+class Template(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("delta", ctypes.c_double),
+                ("f1dot", ctypes.c_double), ("f2dot", ctypes.c_double)]
+
+
+TEMPLATE_DTYPE = np.dtype([("alpha", "<f8"), ("delta", "<f8"), ("f1dot", "<f8"), ("f2dot", "<f8")])
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libfstat.so (once) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FstatLibraryMissing(
+            f"{path} is not built; run paper_2201_00451_gb300.build.build() (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "fstat_plan_create": (i32, [ctypes.POINTER(PlanDesc), ctypes.POINTER(P)]),
+        "fstat_set_data": (i32, [P, i32, P, i32, i64, dbl, P]),
+        "fstat_compute": (i32, [P, P, i64, P, P]),
+        "fstat_freq_axis": (i32, [P, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
+        "fstat_invalidate_sky": (i32, [P]),
+        "fstat_export_sky": (i32, [P, dbl, dbl, P, P, P, P]),
+        "fstat_sync": (i32, [P]),
+        "fstat_set_profiling": (i32, [P, i32]),
+        "fstat_kernel_stats": (i32, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl)]),
+        "fstat_get_split": (i32, [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "fstat_set_split": (i32, [P, i64]),
+        "fstat_plan_destroy": (None, [P]),
+        "fstat_strerror": (ctypes.c_char_p, [i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _strerror(code: int) -> str:
+    try:
+        return load().fstat_strerror(code).decode()
+    except Exception:  # pragma: no cover - only while reporting another error
+        return "?"
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise FstatError(rc, where)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_desc(*, detectors, t0, dt, n_samples, f_het, n_fft, dterms=8, precision=MIXED,
+              t_ref=float("nan"), ephemeris) -> PlanDesc:
+    """Fill a PlanDesc.  ``detectors``: objects with lat, lon, gamma (rad);
+    ``ephemeris``: mapping with the fstat_ephemeris fields."""
+    d = PlanDesc()
+    d.n_det = len(detectors)
+    d.dterms = int(dterms)
+    d.precision = int(precision)
+    d.reserved = 0
+    for X, det in enumerate(detectors):
+        d.det[X] = Detector(det.lat, det.lon, det.gamma)
+    d.t0, d.dt, d.n_samples = float(t0), float(dt), int(n_samples)
+    d.f_het, d.n_fft, d.t_ref = float(f_het), int(n_fft), float(t_ref)
+    for k, _ in Ephemeris._fields_:
+        setattr(d.ephem, k, float(ephemeris[k]))
+    return d
+
+
+def as_templates(templates) -> np.ndarray:
+    """Contiguous structured array of fstat_template records."""
+    a = np.asarray(templates)
+    if a.dtype.names is None:
+        a = np.asarray(a, dtype=np.float64).reshape(-1, 4)
+        out = np.empty(len(a), dtype=TEMPLATE_DTYPE)
+        for k, name in enumerate(TEMPLATE_DTYPE.names):
+            out[name] = a[:, k]
+        return out
+    out = np.empty(len(a), dtype=TEMPLATE_DTYPE)
+    for name in TEMPLATE_DTYPE.names:
+        out[name] = a[name]
+    return out
+
+
+class FstatPlan:
+    """A plan: sample grid, detectors, FFT length, precision (fstat_plan_*)."""
+
+    def __init__(self, desc: PlanDesc):
+        self._lib = load()
+        self._p = ctypes.c_void_p()
+        _check(self._lib.fstat_plan_create(ctypes.byref(desc), ctypes.byref(self._p)), "fstat_plan_create")
+        self.desc = desc
+        self.n_fft = int(desc.n_fft)
+        self.n_samples = int(desc.n_samples)
+
+    @classmethod
+    def from_target(cls, target, precision=MIXED, dterms=None):
+        """Plan for an object exposing the workload fields (detectors, t0, dt,
+        n_samples, f_het, n_fft, dterms, t_ref, ephemeris)."""
+        return cls(make_desc(detectors=target.detectors, t0=target.t0, dt=target.dt,
+                             n_samples=target.n_samples, f_het=target.f_het, n_fft=target.n_fft,
+                             dterms=target.dterms if dterms is None else dterms,
+                             precision=precision, t_ref=target.t_ref, ephemeris=target.ephemeris))
+
+    # -- lifetime
+    def close(self):
+        if self._p:
+            self._lib.fstat_plan_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- data
+    def set_data(self, det: int, xh, sigma: float, stream=None):
+        """fstat_set_data: xh is a numpy array (host) or a CUDA torch tensor of
+        complex64 / complex128 samples."""
+        if isinstance(xh, np.ndarray):
+            x = np.ascontiguousarray(xh)
+            dtype = {np.dtype(np.complex64): C64, np.dtype(np.complex128): C128}[x.dtype]
+            ptr = x.ctypes.data
+            keep = x
+        else:
+            import torch
+            x = xh.contiguous()
+            dtype = {torch.complex64: C64, torch.complex128: C128}[x.dtype]
+            ptr = x.data_ptr()
+            keep = x
+        rc = self._lib.fstat_set_data(self._p, int(det), ctypes.c_void_p(ptr), dtype, int(len(keep)),
+                                      float(sigma), _stream_handle(stream))
+        _check(rc, "fstat_set_data")
+
+    def compute(self, templates, out=None, stream=None):
+        """fstat_compute: returns a CUDA float32 tensor [n_templates, n_fft] of 2F
+        (``out`` may supply it)."""
+        import torch
+        t = as_templates(templates)
+        n = len(t)
+        if out is None:
+            out = torch.empty((n, self.n_fft), dtype=torch.float32, device="cuda")
+        if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() or out.numel() < n * self.n_fft:
+            raise ValueError("out must be a contiguous CUDA float32 tensor with n_templates*n_fft elements")
+        rc = self._lib.fstat_compute(self._p, ctypes.c_void_p(t.ctypes.data), n,
+                                     ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
+        _check(rc, "fstat_compute")
+        return out
+
+    def compute_ptr(self, templates: np.ndarray, out_ptr: int, stream=None):
+        """fstat_compute into a raw device pointer (templates already as TEMPLATE_DTYPE)."""
+        rc = self._lib.fstat_compute(self._p, ctypes.c_void_p(templates.ctypes.data), len(templates),
+                                     ctypes.c_void_p(out_ptr), _stream_handle(stream))
+        _check(rc, "fstat_compute")
+
+    def freq_axis(self):
+        f0, df = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.fstat_freq_axis(self._p, ctypes.byref(f0), ctypes.byref(df)), "fstat_freq_axis")
+        return f0.value, df.value
+
+    def invalidate_sky(self):
+        _check(self._lib.fstat_invalidate_sky(self._p), "fstat_invalidate_sky")
+
+    def export_sky(self, alpha: float, delta: float, stream=None):
+        """Per-sky resampled, antenna-weighted series (G_a, G_b) and (A, B, C, D)."""
+        ga = np.empty(self.n_samples, dtype=np.complex128)
+        gb = np.empty(self.n_samples, dtype=np.complex128)
+        abcd = np.empty(4, dtype=np.float64)
+        rc = self._lib.fstat_export_sky(self._p, float(alpha), float(delta), ctypes.c_void_p(ga.ctypes.data),
+                                        ctypes.c_void_p(gb.ctypes.data), ctypes.c_void_p(abcd.ctypes.data),
+                                        _stream_handle(stream))
+        _check(rc, "fstat_export_sky")
+        return ga, gb, abcd
+
+    def sync(self):
+        _check(self._lib.fstat_sync(self._p), "fstat_sync")
+
+    def set_profiling(self, enable: bool):
+        _check(self._lib.fstat_set_profiling(self._p, int(bool(enable))), "fstat_set_profiling")
+
+    def kernel_stats(self, kernel: int):
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        _check(self._lib.fstat_kernel_stats(self._p, int(kernel), ctypes.byref(n), ctypes.byref(ms)),
+               "fstat_kernel_stats")
+        return n.value, ms.value
+
+    @property
+    def split(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.fstat_get_split(self._p, ctypes.byref(a), ctypes.byref(b)), "fstat_get_split")
+        return a.value, b.value
+
+    def set_split(self, n1: int):
+        _check(self._lib.fstat_set_split(self._p, int(n1)), "fstat_set_split")

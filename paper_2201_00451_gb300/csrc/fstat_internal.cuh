@@ -1,0 +1,117 @@
+// Internal types and device helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fstat.h"
+
+namespace fstat {
+
+// ---------------------------------------------------------------- constants
+constexpr int kMaxDet = FSTAT_MAX_DET;
+constexpr int kSkyBlock = 256;      // threads per block of the per-SSB-sample kernel
+constexpr int kMinLog2 = 5;         // FFT pass lengths 32 .. 4096
+constexpr int kMaxLog2 = 12;
+
+// Per-sky constants, written by k_sky_setup / k_sky_finalize (device memory).
+struct SkyConst {
+  double alpha, delta;
+  double nx, ny, nz;          // unit vector to the source
+  double t_b0;                // start of the SSB grid
+  double j_ref;               // (t_ref - t_b0) / dt
+  // antenna patterns a = sum_i ca[X][i] h_i, b = sum_i cb[X][i] h_i with
+  // h = (1, cos 2H, sin 2H, cos H, sin H), H = alpha - (lon + ph0 + W_rot t)
+  double ca[kMaxDet][5];
+  double cb[kMaxDet][5];
+  double A, B, C, D;
+  double kA, kB, kC;          // 2A/D, 2B/D, 4C/D  (2F = kB|Fa|^2 + kA|Fb|^2 - kC Re FaFb*)
+  float kAf, kBf, kCf;
+};
+
+// Per-template spindown phase polynomial in s = j - J (J = rint(j_ref)):
+// phi(s) = p0 + p1 s + p2 s^2 + p3 s^3 cycles.  Double-float split for the
+// FP32 path (hi + lo carries ~48 bits), FP64 for the FP64 path.
+struct TmplCoef {
+  float hi[4], lo[4];
+  double p[4];
+  int J;
+  int pad_;
+};
+
+// Geometry constants for one plan (kernel argument, by value).
+struct Geo {
+  double c, au, r_earth, w_rot, w_orb, cos_obl, sin_obl, orb_ph0, sid_ph0;
+  double lat[kMaxDet], lon[kMaxDet], gam[kMaxDet];
+  double rcl[kMaxDet], rsl[kMaxDet];   // r_earth cos(lat), r_earth sin(lat)
+  double w[kMaxDet];                   // noise weights 1/(2 sigma^2)
+  double t0, dt, f_het, t_ref;
+  int64_t n;                           // samples per detector
+  int n_det, dterms;
+};
+
+// ---------------------------------------------------- pair of complex values
+// The two transforms Fa and Fb of one template share every index and
+// twiddle, so kernels carry them together: (a.re, a.im, b.re, b.im).
+template <typename T> struct Pair { T ar, ai, br, bi; };
+
+template <typename T> __device__ __forceinline__ Pair<T> padd(const Pair<T>& x, const Pair<T>& y) {
+  return {x.ar + y.ar, x.ai + y.ai, x.br + y.br, x.bi + y.bi};
+}
+template <typename T> __device__ __forceinline__ Pair<T> psub(const Pair<T>& x, const Pair<T>& y) {
+  return {x.ar - y.ar, x.ai - y.ai, x.br - y.br, x.bi - y.bi};
+}
+// multiply both members by the complex number (c, s)
+template <typename T> __device__ __forceinline__ Pair<T> pmul(const Pair<T>& x, T c, T s) {
+  return {x.ar * c - x.ai * s, x.ar * s + x.ai * c, x.br * c - x.bi * s, x.br * s + x.bi * c};
+}
+// multiply by -i
+template <typename T> __device__ __forceinline__ Pair<T> pmul_mi(const Pair<T>& x) {
+  return {x.ai, -x.ar, x.bi, -x.br};
+}
+template <typename T> __device__ __forceinline__ Pair<T> pzero() { return {T(0), T(0), T(0), T(0)}; }
+
+// memory images: float pair = float4 (16 B); double pair = 2 x double2 (32 B)
+template <typename T> struct PairMem;
+template <> struct PairMem<float> { using type = float4; };
+template <> struct PairMem<double> { struct alignas(16) type { double2 a, b; }; };
+
+__device__ __forceinline__ Pair<float> pload(const float4* p) {
+  float4 v = *p; return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ void pstore(float4* p, const Pair<float>& x) {
+  *p = make_float4(x.ar, x.ai, x.br, x.bi);
+}
+__device__ __forceinline__ Pair<double> pload(const PairMem<double>::type* p) {
+  double2 a = p->a, b = p->b; return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void pstore(PairMem<double>::type* p, const Pair<double>& x) {
+  p->a = make_double2(x.ar, x.ai); p->b = make_double2(x.br, x.bi);
+}
+__device__ __forceinline__ Pair<float> pload_g(const float4* __restrict__ p) {
+  float4 v = __ldg(p); return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Pair<double> pload_g(const PairMem<double>::type* __restrict__ p) {
+  double2 a = __ldg(&p->a), b = __ldg(&p->b); return {a.x, a.y, b.x, b.y};
+}
+
+__device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// ------------------------------------------------------------ host helpers
+void launch_sky(const Geo& g, int precision, double alpha, double delta, const void* const* xh,
+                const int* xh_dtype, void* z, void* G, int n1, int64_t lc, double* partials,
+                int n_blocks, SkyConst* sky, int* err, cudaStream_t st);
+void launch_tmpl_coef(const SkyConst* sky, double dt, const fstat_template* tmpl,
+                      const int* order, int first, int count, TmplCoef* out, cudaStream_t st);
+void launch_check_finite(const void* x, int dtype, int64_t n, int* err, cudaStream_t st);
+cudaError_t launch_pass_a_f32(int log2_n2, const void* G, int64_t lc, int64_t n, int n1, int log2N,
+                              const TmplCoef* coef, void* Z, cudaStream_t st);
+cudaError_t launch_pass_b_f32(int log2_n1, const void* Z, int n2, const SkyConst* sky, float* out,
+                              cudaStream_t st);
+cudaError_t launch_pass_a_f64(int log2_n2, const void* G, int64_t lc, int64_t n, int n1, int log2N,
+                              const TmplCoef* coef, void* Z, cudaStream_t st);
+cudaError_t launch_pass_b_f64(int log2_n1, const void* Z, int n2, const SkyConst* sky, float* out,
+                              cudaStream_t st);
+
+}  // namespace fstat

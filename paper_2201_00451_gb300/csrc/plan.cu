@@ -1,0 +1,446 @@
+// C ABI of libfstat: plan lifetime, data upload, template scheduling.
+//
+// fstat_compute groups templates by sky position (alpha, delta).  Per sky it
+// runs the per-sky kernels once (Sec. 3 steps iii-v, which the paper notes
+// are reused across spindown templates, Sec. 4.1), then two FFT kernels per
+// template (steps vi-vii).  Everything is enqueued on the caller's stream;
+// the only host<->device traffic per call is the template list.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "fstat_internal.cuh"
+
+using namespace fstat;
+
+struct EventPair {
+  cudaEvent_t a, b;
+};
+
+struct fstat_plan {
+  fstat_plan_desc d;
+  Geo geo;
+  int device = 0;
+  int log2n = 0, log2n1 = 0, log2n2 = 0;
+  int64_t n1 = 0, n2 = 0, lc = 0;
+  size_t pair_bytes = 16;
+  void* xh[kMaxDet] = {};
+  int dtype[kMaxDet] = {};
+  bool have[kMaxDet] = {};
+  void* z = nullptr;
+  void* G = nullptr;
+  void* Z = nullptr;
+  double* partials = nullptr;
+  int nblk = 0;
+  SkyConst* sky = nullptr;
+  int* d_err = nullptr;   // [0] sticky kernel error, [1] scratch for input checks
+  int* h_err = nullptr;   // pinned
+  fstat_template* d_tmpl = nullptr;
+  int* d_order = nullptr;
+  TmplCoef* d_coef = nullptr;
+  fstat_template* h_tmpl = nullptr;  // pinned staging
+  int* h_order = nullptr;            // pinned staging
+  int64_t cap = 0;
+  cudaEvent_t staged = nullptr;
+  cudaEvent_t done = nullptr;
+  bool staged_pending = false;
+  bool sky_valid = false;
+  double sky_alpha = 0, sky_delta = 0;
+  // profiling (kernel kinds 0 = pass A, 1 = pass B, 2 = per-sky work)
+  bool prof = false;
+  std::vector<EventPair> ev[3];
+  std::vector<EventPair> pool;
+  int64_t launches[3] = {0, 0, 0};
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return FSTAT_OK;
+  if (e == cudaErrorMemoryAllocation) return FSTAT_ERR_OOM;
+  return FSTAT_ERR_CUDA;
+}
+
+#define CK(call)                                 \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+int ilog2_exact(int64_t v) {
+  if (v <= 0 || (v & (v - 1))) return -1;
+  int k = 0;
+  while ((int64_t(1) << k) < v) ++k;
+  return k;
+}
+
+void free_all(fstat_plan* p) {
+  for (int X = 0; X < kMaxDet; ++X) if (p->xh[X]) cudaFree(p->xh[X]);
+  if (p->z) cudaFree(p->z);
+  if (p->G) cudaFree(p->G);
+  if (p->Z) cudaFree(p->Z);
+  if (p->partials) cudaFree(p->partials);
+  if (p->sky) cudaFree(p->sky);
+  if (p->d_err) cudaFree(p->d_err);
+  if (p->h_err) cudaFreeHost(p->h_err);
+  if (p->d_tmpl) cudaFree(p->d_tmpl);
+  if (p->d_order) cudaFree(p->d_order);
+  if (p->d_coef) cudaFree(p->d_coef);
+  if (p->h_tmpl) cudaFreeHost(p->h_tmpl);
+  if (p->h_order) cudaFreeHost(p->h_order);
+  if (p->staged) cudaEventDestroy(p->staged);
+  if (p->done) cudaEventDestroy(p->done);
+  for (auto& v : p->ev)
+    for (auto& e : v) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  for (auto& e : p->pool) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+}
+
+int ensure_capacity(fstat_plan* p, int64_t n) {
+  if (n <= p->cap) return FSTAT_OK;
+  if (p->staged_pending) { CK(cudaEventSynchronize(p->staged)); p->staged_pending = false; }
+  CK(cudaDeviceSynchronize());
+  int64_t c = std::max<int64_t>(n, std::max<int64_t>(1024, 2 * p->cap));
+  if (p->d_tmpl) cudaFree(p->d_tmpl);
+  if (p->d_order) cudaFree(p->d_order);
+  if (p->d_coef) cudaFree(p->d_coef);
+  if (p->h_tmpl) cudaFreeHost(p->h_tmpl);
+  if (p->h_order) cudaFreeHost(p->h_order);
+  p->d_tmpl = nullptr; p->d_order = nullptr; p->d_coef = nullptr; p->h_tmpl = nullptr; p->h_order = nullptr;
+  p->cap = 0;
+  CK(cudaMalloc(&p->d_tmpl, c * sizeof(fstat_template)));
+  CK(cudaMalloc(&p->d_order, c * sizeof(int)));
+  CK(cudaMalloc(&p->d_coef, c * sizeof(TmplCoef)));
+  CK(cudaMallocHost(&p->h_tmpl, c * sizeof(fstat_template)));
+  CK(cudaMallocHost(&p->h_order, c * sizeof(int)));
+  p->cap = c;
+  return FSTAT_OK;
+}
+
+EventPair get_events(fstat_plan* p) {
+  if (!p->pool.empty()) { EventPair e = p->pool.back(); p->pool.pop_back(); return e; }
+  EventPair e{};
+  cudaEventCreate(&e.a);
+  cudaEventCreate(&e.b);
+  return e;
+}
+
+int run_sky(fstat_plan* p, double alpha, double delta, cudaStream_t st) {
+  EventPair e{};
+  if (p->prof) { e = get_events(p); cudaEventRecord(e.a, st); }
+  const void* xh[kMaxDet];
+  for (int X = 0; X < kMaxDet; ++X) xh[X] = p->xh[X];
+  launch_sky(p->geo, p->d.precision, alpha, delta, xh, p->dtype, p->z, p->G, (int)p->n1, p->lc,
+             p->partials, p->nblk, p->sky, p->d_err, st);
+  CK(cudaGetLastError());
+  if (p->prof) { cudaEventRecord(e.b, st); p->ev[2].push_back(e); p->launches[2]++; }
+  p->sky_valid = true;
+  p->sky_alpha = alpha;
+  p->sky_delta = delta;
+  return FSTAT_OK;
+}
+
+int set_split(fstat_plan* p, int log2n1) {
+  int log2n2 = p->log2n - log2n1;
+  if (log2n1 < kMinLog2 || log2n1 > kMaxLog2 || log2n2 < kMinLog2 || log2n2 > kMaxLog2)
+    return FSTAT_ERR_UNSUPPORTED;
+  p->log2n1 = log2n1;
+  p->log2n2 = log2n2;
+  p->n1 = int64_t(1) << log2n1;
+  p->n2 = int64_t(1) << log2n2;
+  p->lc = (p->d.n_samples + p->n1 - 1) / p->n1;
+  p->sky_valid = false;
+  return FSTAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fstat_strerror(int code) {
+  switch (code) {
+    case FSTAT_OK: return "ok";
+    case FSTAT_ERR_INVALID_ARG: return "invalid argument";
+    case FSTAT_ERR_OOM: return "out of memory";
+    case FSTAT_ERR_CUDA: return "CUDA error";
+    case FSTAT_ERR_DEGENERATE: return "degenerate antenna-pattern matrix (D <= 0)";
+    case FSTAT_ERR_NONFINITE: return "non-finite value in input series";
+    case FSTAT_ERR_NOT_READY: return "not every detector has data";
+    case FSTAT_ERR_UNSUPPORTED: return "size outside the supported range";
+    default: return "unknown error";
+  }
+}
+
+int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
+  if (!desc || !out) return FSTAT_ERR_INVALID_ARG;
+  *out = nullptr;
+  const fstat_plan_desc& d = *desc;
+  if (d.n_det < 1 || d.n_det > FSTAT_MAX_DET || d.dterms < 1 || d.dterms > 32 ||
+      (d.precision != FSTAT_MIXED && d.precision != FSTAT_FP64) || d.reserved != 0 ||
+      !(d.dt > 0.0) || !std::isfinite(d.t0) || !std::isfinite(d.f_het) || d.n_samples < 1 ||
+      d.n_samples >= (int64_t(1) << 24) || !(d.ephem.c > 0.0))
+    return FSTAT_ERR_INVALID_ARG;
+  int log2n = ilog2_exact(d.n_fft);
+  if (log2n < 0) return FSTAT_ERR_INVALID_ARG;
+  if (log2n < 2 * kMinLog2 || log2n > 2 * kMaxLog2) return FSTAT_ERR_UNSUPPORTED;
+  if (d.n_fft < d.n_samples) return FSTAT_ERR_INVALID_ARG;
+
+  fstat_plan* p = new (std::nothrow) fstat_plan();
+  if (!p) return FSTAT_ERR_OOM;
+  p->d = d;
+  cudaGetDevice(&p->device);
+  p->log2n = log2n;
+  set_split(p, log2n / 2);
+  p->pair_bytes = d.precision == FSTAT_FP64 ? 32 : 16;
+
+  Geo& g = p->geo;
+  std::memset(&g, 0, sizeof(g));
+  g.c = d.ephem.c;
+  g.au = d.ephem.au;
+  g.r_earth = d.ephem.r_earth;
+  g.w_rot = d.ephem.omega_rot;
+  g.w_orb = d.ephem.omega_orb;
+  g.cos_obl = std::cos(d.ephem.obliquity);
+  g.sin_obl = std::sin(d.ephem.obliquity);
+  g.orb_ph0 = d.ephem.orb_phase0;
+  g.sid_ph0 = d.ephem.sidereal_phase0;
+  for (int X = 0; X < d.n_det; ++X) {
+    g.lat[X] = d.det[X].lat_rad;
+    g.lon[X] = d.det[X].lon_rad;
+    g.gam[X] = d.det[X].gamma_rad;
+    g.rcl[X] = d.ephem.r_earth * std::cos(d.det[X].lat_rad);
+    g.rsl[X] = d.ephem.r_earth * std::sin(d.det[X].lat_rad);
+    g.w[X] = 0.0;
+  }
+  g.t0 = d.t0;
+  g.dt = d.dt;
+  g.f_het = d.f_het;
+  g.t_ref = std::isnan(d.t_ref) ? d.t0 + (double)(d.n_samples / 2) * d.dt : d.t_ref;
+  g.n = d.n_samples;
+  g.n_det = d.n_det;
+  g.dterms = d.dterms;
+
+  const int64_t N = d.n_samples;
+  const size_t zb = d.precision == FSTAT_FP64 ? 16 : 8;
+  p->nblk = (int)((N + kSkyBlock - 1) / kSkyBlock);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&p->z, (size_t)d.n_det * N * zb);
+  if (e == cudaSuccess) e = cudaMalloc(&p->G, (size_t)(N + (int64_t(1) << kMaxLog2)) * p->pair_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->Z, (size_t)d.n_fft * p->pair_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->partials, (size_t)3 * p->nblk * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->sky, sizeof(SkyConst));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_err, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_err, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->staged, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_all(p);
+    delete p;
+    return cuda_status(e);
+  }
+  *out = p;
+  return FSTAT_OK;
+}
+
+void fstat_plan_destroy(fstat_plan* p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  free_all(p);
+  delete p;
+}
+
+int fstat_set_data(fstat_plan* p, int det, const void* xh, int dtype, int64_t n, double sigma,
+                   void* stream) {
+  if (!p || !xh || det < 0 || det >= p->d.n_det || n != p->d.n_samples || !(sigma > 0.0) ||
+      !std::isfinite(sigma) || (dtype != FSTAT_C64 && dtype != FSTAT_C128))
+    return FSTAT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t eb = dtype == FSTAT_C128 ? 16 : 8;
+  if (p->xh[det] && p->dtype[det] != dtype) {
+    CK(cudaStreamSynchronize(st));
+    cudaFree(p->xh[det]);
+    p->xh[det] = nullptr;
+  }
+  if (!p->xh[det]) CK(cudaMalloc(&p->xh[det], (size_t)n * eb));
+  p->dtype[det] = dtype;
+  p->have[det] = false;
+  p->sky_valid = false;
+  CK(cudaMemcpyAsync(p->xh[det], xh, (size_t)n * eb, cudaMemcpyDefault, st));
+  CK(cudaMemsetAsync(p->d_err + 1, 0, sizeof(int), st));
+  launch_check_finite(p->xh[det], dtype, n, p->d_err + 1, st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(p->h_err + 1, p->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (p->h_err[1] != 0) return p->h_err[1];
+  p->geo.w[det] = 1.0 / (2.0 * sigma * sigma);
+  p->have[det] = true;
+  return FSTAT_OK;
+}
+
+int fstat_compute(fstat_plan* p, const fstat_template* tmpl, int64_t n_tmpl, float* twoF,
+                  void* stream) {
+  if (!p || n_tmpl < 0 || (n_tmpl > 0 && (!tmpl || !twoF))) return FSTAT_ERR_INVALID_ARG;
+  if (n_tmpl > INT32_MAX) return FSTAT_ERR_INVALID_ARG;
+  for (int X = 0; X < p->d.n_det; ++X)
+    if (!p->have[X]) return FSTAT_ERR_NOT_READY;
+  for (int64_t i = 0; i < n_tmpl; ++i)
+    if (!std::isfinite(tmpl[i].alpha) || !std::isfinite(tmpl[i].delta) ||
+        !std::isfinite(tmpl[i].f1dot) || !std::isfinite(tmpl[i].f2dot))
+      return FSTAT_ERR_INVALID_ARG;
+  if (n_tmpl == 0) return FSTAT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = ensure_capacity(p, n_tmpl);
+  if (rc) return rc;
+  if (p->staged_pending) { CK(cudaEventSynchronize(p->staged)); p->staged_pending = false; }
+
+  std::memcpy(p->h_tmpl, tmpl, (size_t)n_tmpl * sizeof(fstat_template));
+  int* ord = p->h_order;
+  std::iota(ord, ord + n_tmpl, 0);
+  std::stable_sort(ord, ord + n_tmpl, [&](int a, int b) {
+    if (tmpl[a].alpha != tmpl[b].alpha) return tmpl[a].alpha < tmpl[b].alpha;
+    return tmpl[a].delta < tmpl[b].delta;
+  });
+  CK(cudaMemcpyAsync(p->d_tmpl, p->h_tmpl, (size_t)n_tmpl * sizeof(fstat_template),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(p->d_order, p->h_order, (size_t)n_tmpl * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(p->staged, st));
+  p->staged_pending = true;
+
+  const int64_t nfft = p->d.n_fft;
+  int64_t i = 0;
+  while (i < n_tmpl) {
+    const fstat_template& t0 = tmpl[ord[i]];
+    int64_t j = i + 1;
+    while (j < n_tmpl && tmpl[ord[j]].alpha == t0.alpha && tmpl[ord[j]].delta == t0.delta) ++j;
+    if (!(p->sky_valid && p->sky_alpha == t0.alpha && p->sky_delta == t0.delta)) {
+      rc = run_sky(p, t0.alpha, t0.delta, st);
+      if (rc) return rc;
+    }
+    launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, (int)i, (int)(j - i), p->d_coef, st);
+    CK(cudaGetLastError());
+    for (int64_t k = i; k < j; ++k) {
+      float* out = twoF + (int64_t)ord[k] * nfft;
+      const TmplCoef* coef = p->d_coef + k;
+      EventPair ea{}, eb{};
+      if (p->prof) { ea = get_events(p); cudaEventRecord(ea.a, st); }
+      cudaError_t e = p->d.precision == FSTAT_FP64
+          ? launch_pass_a_f64(p->log2n2, p->G, p->lc, p->d.n_samples, (int)p->n1, p->log2n, coef, p->Z, st)
+          : launch_pass_a_f32(p->log2n2, p->G, p->lc, p->d.n_samples, (int)p->n1, p->log2n, coef, p->Z, st);
+      if (e != cudaSuccess) return cuda_status(e);
+      if (p->prof) {
+        cudaEventRecord(ea.b, st); p->ev[0].push_back(ea); p->launches[0]++;
+        eb = get_events(p); cudaEventRecord(eb.a, st);
+      }
+      e = p->d.precision == FSTAT_FP64
+          ? launch_pass_b_f64(p->log2n1, p->Z, (int)p->n2, p->sky, out, st)
+          : launch_pass_b_f32(p->log2n1, p->Z, (int)p->n2, p->sky, out, st);
+      if (e != cudaSuccess) return cuda_status(e);
+      if (p->prof) { cudaEventRecord(eb.b, st); p->ev[1].push_back(eb); p->launches[1]++; }
+    }
+    i = j;
+  }
+  CK(cudaEventRecord(p->done, st));
+  return FSTAT_OK;
+}
+
+int fstat_freq_axis(const fstat_plan* p, double* f0, double* df) {
+  if (!p || !f0 || !df) return FSTAT_ERR_INVALID_ARG;
+  *df = 1.0 / ((double)p->d.n_fft * p->d.dt);
+  *f0 = p->d.f_het - (double)(p->d.n_fft / 2) * *df;
+  return FSTAT_OK;
+}
+
+int fstat_invalidate_sky(fstat_plan* p) {
+  if (!p) return FSTAT_ERR_INVALID_ARG;
+  p->sky_valid = false;
+  return FSTAT_OK;
+}
+
+int fstat_sync(fstat_plan* p) {
+  if (!p) return FSTAT_ERR_INVALID_ARG;
+  CK(cudaEventSynchronize(p->done));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(p->h_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  int e = p->h_err[0];
+  if (e) CK(cudaMemset(p->d_err, 0, sizeof(int)));
+  return e;
+}
+
+int fstat_export_sky(fstat_plan* p, double alpha, double delta, double* ga, double* gb,
+                     double* abcd, void* stream) {
+  if (!p || !std::isfinite(alpha) || !std::isfinite(delta)) return FSTAT_ERR_INVALID_ARG;
+  for (int X = 0; X < p->d.n_det; ++X)
+    if (!p->have[X]) return FSTAT_ERR_NOT_READY;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = run_sky(p, alpha, delta, st);
+  if (rc) return rc;
+  const int64_t N = p->d.n_samples;
+  std::vector<unsigned char> buf((size_t)(p->n1 * p->lc) * p->pair_bytes);
+  CK(cudaMemcpyAsync(buf.data(), p->G, buf.size(), cudaMemcpyDeviceToHost, st));
+  SkyConst sc;
+  CK(cudaMemcpyAsync(&sc, p->sky, sizeof(sc), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int64_t j = 0; j < N; ++j) {
+    int64_t pos = (j % p->n1) * p->lc + j / p->n1;
+    double v[4];
+    if (p->pair_bytes == 16) {
+      const float* f = reinterpret_cast<const float*>(buf.data()) + 4 * pos;
+      for (int q = 0; q < 4; ++q) v[q] = f[q];
+    } else {
+      const double* f = reinterpret_cast<const double*>(buf.data()) + 4 * pos;
+      for (int q = 0; q < 4; ++q) v[q] = f[q];
+    }
+    if (ga) { ga[2 * j] = v[0]; ga[2 * j + 1] = v[1]; }
+    if (gb) { gb[2 * j] = v[2]; gb[2 * j + 1] = v[3]; }
+  }
+  if (abcd) { abcd[0] = sc.A; abcd[1] = sc.B; abcd[2] = sc.C; abcd[3] = sc.D; }
+  return FSTAT_OK;
+}
+
+int fstat_set_profiling(fstat_plan* p, int enable) {
+  if (!p) return FSTAT_ERR_INVALID_ARG;
+  CK(cudaDeviceSynchronize());
+  for (auto& v : p->ev) {
+    for (auto& e : v) p->pool.push_back(e);
+    v.clear();
+  }
+  for (auto& l : p->launches) l = 0;
+  p->prof = enable != 0;
+  return FSTAT_OK;
+}
+
+int fstat_kernel_stats(fstat_plan* p, int kernel, int64_t* launches, double* total_ms) {
+  if (!p || kernel < 0 || kernel > 2 || !launches || !total_ms) return FSTAT_ERR_INVALID_ARG;
+  CK(cudaDeviceSynchronize());
+  double tot = 0.0;
+  for (auto& e : p->ev[kernel]) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e.a, e.b));
+    tot += ms;
+  }
+  *launches = p->launches[kernel];
+  *total_ms = tot;
+  return FSTAT_OK;
+}
+
+int fstat_get_split(const fstat_plan* p, int64_t* n1, int64_t* n2) {
+  if (!p || !n1 || !n2) return FSTAT_ERR_INVALID_ARG;
+  *n1 = p->n1;
+  *n2 = p->n2;
+  return FSTAT_OK;
+}
+
+int fstat_set_split(fstat_plan* p, int64_t n1) {
+  if (!p) return FSTAT_ERR_INVALID_ARG;
+  int l = ilog2_exact(n1);
+  if (l < 0) return FSTAT_ERR_INVALID_ARG;
+  CK(cudaDeviceSynchronize());
+  return set_split(p, l);
+}
+
+}  // extern "C"

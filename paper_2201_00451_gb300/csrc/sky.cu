@@ -1,0 +1,318 @@
+// Per-sky kernels: Sec. 3 steps (iii), (iv), (v) of the resampling method,
+// antenna weighting, the noise-weighted detector sum, and the antenna-pattern
+// integrals A, B, C, D of eq. (Fstat).  The result G = (G_a, G_b) is stored
+// in the column-major layout the FFT pass A reads: element j goes to
+// G[(j mod n1) * lc + j / n1].
+//
+// Timing (t_m, the inversion T + t_m(T) = t_b, u = (T - t0)/dt) is FP64 in
+// both precisions; f_h t_m is reduced mod 1 in FP64 before the sincos.
+
+#include <math.h>
+
+#include "fstat_internal.cuh"
+
+namespace fstat {
+
+namespace {
+
+struct Rot { double c, s; };  // cos, sin of the detector's sidereal angle
+
+// Roemer delay t_m(t) = (r_orb + r_rot) . n / c  (Sec. 2 phase model).
+__device__ __forceinline__ double roemer(const Geo& g, const SkyConst& s, int X, double t, Rot* r) {
+  double so, co;
+  sincos(g.orb_ph0 + g.w_orb * t, &so, &co);
+  double orb = g.au * (co * s.nx + so * (g.cos_obl * s.ny + g.sin_obl * s.nz));
+  double sp, cp;
+  sincos(g.lon[X] + g.sid_ph0 + g.w_rot * t, &sp, &cp);
+  double rot = g.rcl[X] * (cp * s.nx + sp * s.ny) + g.rsl[X] * s.nz;
+  r->c = cp;
+  r->s = sp;
+  return (orb + rot) / g.c;
+}
+
+// a(t), b(t) from the harmonic coefficients and the sidereal angle (JKS 1998
+// eqs. 12-13): H = alpha - phi, h = (1, cos 2H, sin 2H, cos H, sin H).
+__device__ __forceinline__ void antenna(const SkyConst& s, int X, const Rot& r, double* a, double* b) {
+  double ca = cos(s.alpha), sa = sin(s.alpha);
+  double cH = ca * r.c + sa * r.s;
+  double sH = sa * r.c - ca * r.s;
+  double c2H = cH * cH - sH * sH;
+  double s2H = 2.0 * sH * cH;
+  *a = s.ca[X][0] + s.ca[X][1] * c2H + s.ca[X][2] * s2H + s.ca[X][3] * cH + s.ca[X][4] * sH;
+  *b = s.cb[X][0] + s.cb[X][1] * c2H + s.cb[X][2] * s2H + s.cb[X][3] * cH + s.cb[X][4] * sH;
+}
+
+__global__ void k_sky_setup(Geo g, double alpha, double delta, SkyConst* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  SkyConst s;
+  s.alpha = alpha;
+  s.delta = delta;
+  s.nx = cos(delta) * cos(alpha);
+  s.ny = cos(delta) * sin(alpha);
+  s.nz = sin(delta);
+  // SSB grid start: t0 + orbital Roemer delay at the data midpoint
+  double t_mid = g.t0 + 0.5 * (double)g.n * g.dt;
+  double so, co;
+  sincos(g.orb_ph0 + g.w_orb * t_mid, &so, &co);
+  double orb = g.au * (co * s.nx + so * (g.cos_obl * s.ny + g.sin_obl * s.nz));
+  s.t_b0 = g.t0 + orb / g.c;
+  s.j_ref = (g.t_ref - s.t_b0) / g.dt;
+  double sd = sin(delta), cd = cos(delta), s2d = sin(2.0 * delta), c2d = cos(2.0 * delta);
+  for (int X = 0; X < kMaxDet; ++X) {
+    for (int i = 0; i < 5; ++i) { s.ca[X][i] = 0.0; s.cb[X][i] = 0.0; }
+    if (X >= g.n_det) continue;
+    double lam = g.lat[X], gam = g.gam[X];
+    double s2g = sin(2.0 * gam), c2g = cos(2.0 * gam);
+    double sl = sin(lam), cl = cos(lam), s2l = sin(2.0 * lam), c2l = cos(2.0 * lam);
+    s.ca[X][0] = 0.75 * s2g * cl * cl * cd * cd;
+    s.ca[X][1] = s2g * (3.0 - c2l) * (3.0 - c2d) / 16.0;
+    s.ca[X][2] = -0.25 * c2g * sl * (3.0 - c2d);
+    s.ca[X][3] = 0.25 * s2g * s2l * s2d;
+    s.ca[X][4] = -0.5 * c2g * cl * s2d;
+    s.cb[X][0] = 0.0;
+    s.cb[X][1] = c2g * sl * sd;
+    s.cb[X][2] = 0.25 * s2g * (3.0 - c2l) * sd;
+    s.cb[X][3] = c2g * cl * cd;
+    s.cb[X][4] = 0.5 * s2g * s2l * cd;
+  }
+  s.A = s.B = s.C = s.D = 0.0;
+  s.kA = s.kB = s.kC = 0.0;
+  s.kAf = s.kBf = s.kCf = 0.0f;
+  *out = s;
+}
+
+// Step (iii): z = x_h exp(-i 2 pi frac(f_h t_m(t_k))).
+template <typename TIn, typename TZ>
+__global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* __restrict__ z,
+                                 const SkyConst* __restrict__ skyp) {
+  const SkyConst& s = *skyp;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < g.n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double t = g.t0 + (double)k * g.dt;
+    Rot r;
+    double ph = g.f_het * roemer(g, s, X, t, &r);
+    ph -= floor(ph);
+    TIn x = xh[k];
+    if constexpr (sizeof(TZ) == sizeof(float2)) {
+      float sn, cs;
+      sincospif(2.0f * (float)ph, &sn, &cs);
+      float xr = (float)x.x, xi = (float)x.y;
+      z[k] = make_float2(xr * cs + xi * sn, xi * cs - xr * sn);
+    } else {
+      double sn, cs;
+      sincospi(2.0 * ph, &sn, &cs);
+      double xr = (double)x.x, xi = (double)x.y;
+      z[k] = make_double2(xr * cs + xi * sn, xi * cs - xr * sn);
+    }
+  }
+}
+
+// Steps (iv) + (v) + antenna weighting + detector sum, one SSB sample per thread.
+template <typename T, typename TZ>
+__global__ void __launch_bounds__(kSkyBlock)
+k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
+           typename PairMem<T>::type* __restrict__ G, int n1, int64_t lc, double* __restrict__ partials) {
+  const SkyConst& s = *skyp;
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double sa = 0.0, sb = 0.0, sab = 0.0;
+  if (j < g.n) {
+    double tb = s.t_b0 + (double)j * g.dt;
+    Pair<T> acc = pzero<T>();
+    const int D = g.dterms;
+    const T nT = (T)g.n;
+    for (int X = 0; X < g.n_det; ++X) {
+      Rot r;
+      double T_ = tb - roemer(g, s, X, tb, &r);
+#pragma unroll 1
+      for (int it = 0; it < 3; ++it) T_ = tb - roemer(g, s, X, T_, &r);
+      double u = (T_ - g.t0) / g.dt;
+      long long k0 = __double2ll_rn(u);
+      if (k0 < 0 || k0 > g.n - 1) continue;
+      double dl = u - (double)k0;
+      const TZ* zx = z + (int64_t)X * g.n;
+      T zr = 0, zi = 0;
+      if (dl == 0.0) {
+        TZ v = zx[k0];
+        zr = (T)v.x;
+        zi = (T)v.y;
+      } else {
+        T d = (T)dl, sd, cd_;
+        sincospi_t(d, &sd, &cd_);
+        const T inv_taper = (T)1 / (T)(D + 1);
+        for (int m = -D; m <= D; ++m) {
+          long long k = k0 + m;
+          if (k < 0 || k >= g.n) continue;
+          T x = d - (T)m;
+          T sx, cx, st, ct;
+          sincospi_t(x / nT, &sx, &cx);
+          sincospi_t(x * inv_taper, &st, &ct);
+          T num = (m & 1) ? -sd : sd;  // sin(pi (d - m)) = (-1)^m sin(pi d)
+          T wgt = num / (nT * sx) * ((T)0.54 + (T)0.46 * ct);
+          TZ v = zx[k];
+          zr += (T)v.x * wgt;
+          zi += (T)v.y * wgt;
+        }
+      }
+      double a, b;
+      antenna(s, X, r, &a, &b);
+      double w = g.w[X];
+      T wa = (T)(w * a), wb = (T)(w * b);
+      acc.ar += wa * zr;
+      acc.ai += wa * zi;
+      acc.br += wb * zr;
+      acc.bi += wb * zi;
+      sa += w * a * a;
+      sb += w * b * b;
+      sab += w * a * b;
+    }
+    int64_t n1i = j % n1, n2i = j / n1;
+    pstore(G + n1i * lc + n2i, acc);
+  }
+  // block reduction of the A, B, C partial sums (fixed order)
+  __shared__ double red[3][kSkyBlock / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_down_sync(0xffffffffu, sa, o);
+    sb += __shfl_down_sync(0xffffffffu, sb, o);
+    sab += __shfl_down_sync(0xffffffffu, sab, o);
+  }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { red[0][wid] = sa; red[1][wid] = sb; red[2][wid] = sab; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double A = 0, B = 0, C = 0;
+    for (int i = 0; i < kSkyBlock / 32; ++i) { A += red[0][i]; B += red[1][i]; C += red[2][i]; }
+    partials[3 * blockIdx.x + 0] = A;
+    partials[3 * blockIdx.x + 1] = B;
+    partials[3 * blockIdx.x + 2] = C;
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+k_sky_finalize(const double* __restrict__ partials, int nblocks, SkyConst* sky, int* err) {
+  __shared__ double red[3][1024];
+  double A = 0, B = 0, C = 0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    A += partials[3 * i + 0];
+    B += partials[3 * i + 1];
+    C += partials[3 * i + 2];
+  }
+  red[0][threadIdx.x] = A;
+  red[1][threadIdx.x] = B;
+  red[2][threadIdx.x] = C;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+      red[2][threadIdx.x] += red[2][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    A = red[0][0];
+    B = red[1][0];
+    C = red[2][0];
+    double D = A * B - C * C;
+    sky->A = A;
+    sky->B = B;
+    sky->C = C;
+    sky->D = D;
+    bool ok = isfinite(D) && D > 1e-12 * A * B && A > 0.0 && B > 0.0;
+    if (!ok) {
+      atomicCAS(err, 0, FSTAT_ERR_DEGENERATE);
+      D = 1.0;
+      A = B = C = 0.0;
+    }
+    sky->kA = 2.0 * A / D;
+    sky->kB = 2.0 * B / D;
+    sky->kC = 4.0 * C / D;
+    sky->kAf = (float)sky->kA;
+    sky->kBf = (float)sky->kB;
+    sky->kCf = (float)sky->kC;
+  }
+}
+
+// Per-template spindown polynomial in s = j - J (see TmplCoef).
+__global__ void k_tmpl_coef(const SkyConst* __restrict__ sky, double dt,
+                            const fstat_template* __restrict__ tmpl, const int* __restrict__ order,
+                            int first, int count, TmplCoef* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const fstat_template tp = tmpl[order[first + i]];
+  double jr = sky->j_ref;
+  double J = rint(jr);
+  double e = jr - J;
+  double c2 = tp.f1dot * dt * dt / 2.0;
+  double c3 = tp.f2dot * dt * dt * dt / 6.0;
+  TmplCoef c;
+  c.p[3] = c3;
+  c.p[2] = c2 - 3.0 * c3 * e;
+  c.p[1] = -2.0 * c2 * e + 3.0 * c3 * e * e;
+  c.p[0] = c2 * e * e - c3 * e * e * e;
+  for (int q = 0; q < 4; ++q) {
+    float h = (float)c.p[q];
+    c.hi[q] = h;
+    c.lo[q] = (float)(c.p[q] - (double)h);
+  }
+  c.J = (int)J;
+  c.pad_ = 0;
+  out[first + i] = c;
+}
+
+template <typename TIn, typename TZ>
+void launch_phase(const Geo& g, int X, const void* xh, void* z, const SkyConst* sky, cudaStream_t st) {
+  int blocks = (int)((g.n + 255) / 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_detector_phase<TIn, TZ><<<blocks, 256, 0, st>>>(g, X, (const TIn*)xh, (TZ*)z + (int64_t)X * g.n, sky);
+}
+
+}  // namespace
+
+void launch_sky(const Geo& g, int precision, double alpha, double delta, const void* const* xh,
+                const int* xh_dtype, void* z, void* G, int n1, int64_t lc, double* partials,
+                int n_blocks, SkyConst* sky, int* err, cudaStream_t st) {
+  k_sky_setup<<<1, 32, 0, st>>>(g, alpha, delta, sky);
+  for (int X = 0; X < g.n_det; ++X) {
+    bool in64 = xh_dtype[X] == FSTAT_C128;
+    if (precision == FSTAT_FP64) {
+      if (in64) launch_phase<double2, double2>(g, X, xh[X], z, sky, st);
+      else launch_phase<float2, double2>(g, X, xh[X], z, sky, st);
+    } else {
+      if (in64) launch_phase<double2, float2>(g, X, xh[X], z, sky, st);
+      else launch_phase<float2, float2>(g, X, xh[X], z, sky, st);
+    }
+  }
+  if (precision == FSTAT_FP64) {
+    k_resample<double, double2><<<n_blocks, kSkyBlock, 0, st>>>(
+        g, sky, (const double2*)z, (PairMem<double>::type*)G, n1, lc, partials);
+  } else {
+    k_resample<float, float2><<<n_blocks, kSkyBlock, 0, st>>>(
+        g, sky, (const float2*)z, (float4*)G, n1, lc, partials);
+  }
+  k_sky_finalize<<<1, 1024, 0, st>>>(partials, n_blocks, sky, err);
+}
+
+void launch_tmpl_coef(const SkyConst* sky, double dt, const fstat_template* tmpl,
+                         const int* order, int first, int count, TmplCoef* out, cudaStream_t st) {
+  if (count <= 0) return;
+  k_tmpl_coef<<<(count + 127) / 128, 128, 0, st>>>(sky, dt, tmpl, order, first, count, out);
+}
+
+// Scan an input series for NaN/Inf.
+template <typename TIn>
+__global__ void k_check_finite(const TIn* __restrict__ x, int64_t n, int* err) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    TIn v = x[k];
+    if (!isfinite((double)v.x) || !isfinite((double)v.y)) atomicCAS(err, 0, FSTAT_ERR_NONFINITE);
+  }
+}
+
+void launch_check_finite(const void* x, int dtype, int64_t n, int* err, cudaStream_t st) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (dtype == FSTAT_C128) k_check_finite<double2><<<blocks, 256, 0, st>>>((const double2*)x, n, err);
+  else k_check_finite<float2><<<blocks, 256, 0, st>>>((const float2*)x, n, err);
+}
+
+}  // namespace fstat
