@@ -153,6 +153,32 @@ int fstat_kernel_stats(fstat_plan* plan, int kernel, int64_t* launches, double* 
 int fstat_get_split(const fstat_plan* plan, int64_t* n1, int64_t* n2);
 int fstat_set_split(fstat_plan* plan, int64_t n1);
 
+/* 2F for one template from a caller-supplied resampled series, allocating
+ * nothing.  The paper has no counterpart: this exists for callers that may
+ * not call cudaMalloc (a plug-in inside an application whose memory pool
+ * owns the device memory, or a pipeline that must not allocate after
+ * start-up).  Its scratch memory is a fixed file-scope device array of
+ * 8.1 MB, reserved on every GPU that loads the library until exit.
+ *   g_pairs   DEVICE, n_samples float4 (Ga.re, Ga.im, Gb.re, Gb.im) in SSB
+ *             sample order j (the detector-summed, antenna-weighted series
+ *             G_a, G_b; fstat_export_sky returns them), 16-byte aligned
+ *   n_samples 1..n_fft;  n_fft: power of two, 2^10..2^18 (larger sizes
+ *             return FSTAT_ERR_UNSUPPORTED)
+ *   dt, tau0  sample spacing; SSB time of sample 0 minus the spindown
+ *             reference time, so tau_j = tau0 + j dt
+ *   A, B, C   antenna-pattern integrals of the series (D = AB - C^2 > 0)
+ *   twoF      DEVICE output, n_fft floats, ascending frequency
+ * Every call shares the scratch array, which keeps the previous call's
+ * contents (nothing in it needs to start at zero); calls that overlap on
+ * the GPU (different streams, or different host threads) race on it.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Errors: INVALID_ARG, UNSUPPORTED, DEGENERATE,
+ * CUDA. */
+int fstat_twoF_noalloc(const void* g_pairs, int64_t n_samples, int64_t n_fft, double dt, double tau0,
+                       double A, double B, double C, double f1dot, double f2dot, float* twoF,
+                       void* stream);
+
 void fstat_plan_destroy(fstat_plan* plan);
 const char* fstat_strerror(int code);
 

@@ -41,7 +41,7 @@ EXPORTS = (
     "fstat_plan_create", "fstat_set_data", "fstat_compute", "fstat_freq_axis",
     "fstat_invalidate_sky", "fstat_export_sky", "fstat_sync", "fstat_set_profiling",
     "fstat_kernel_stats", "fstat_get_split", "fstat_set_split", "fstat_plan_destroy",
-    "fstat_strerror",
+    "fstat_strerror", "fstat_twoF_noalloc",
 )
 
 
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fstat_set_split": (i32, [P, i64]),
         "fstat_plan_destroy": (None, [P]),
         "fstat_strerror": (ctypes.c_char_p, [i32]),
+        "fstat_twoF_noalloc": (i32, [P, i64, i64, dbl, dbl, dbl, dbl, dbl, dbl, dbl, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

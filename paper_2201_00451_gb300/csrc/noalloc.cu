@@ -1,0 +1,151 @@
+// fstat_twoF_noalloc: one template's 2F from a caller-resampled series,
+// without any device allocation.
+//
+// Some callers cannot call cudaMalloc: a plug-in running inside a host
+// application whose memory pool already owns the device memory and forbids
+// outside allocations, and a low-latency pipeline that must not allocate
+// after start-up because cudaMalloc can synchronise the device and has no
+// latency bound.  This entry point keeps its working memory in file-scope
+// __device__ arrays of fixed size, reserved when the library is loaded
+// (every GPU that loads libfstat holds them until the process exits).
+//
+// It runs the same FFT pass kernels as fstat_compute (spindown phase +
+// column FFTs, then row FFTs + eq. Fstat); only the scratch memory differs.
+
+#include <math.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "fstat_internal.cuh"
+
+namespace fstat {
+namespace {
+
+constexpr int kNoallocMaxLog2 = 18;  // n_fft <= 2^18
+constexpr int64_t kNoallocMaxFft = int64_t(1) << kNoallocMaxLog2;
+constexpr int64_t kNoallocGElems = kNoallocMaxFft + (int64_t(1) << kMaxLog2);
+
+// Scratch: column-major copy of the input pairs, the FFT intermediate, and
+// the per-call constants.  4.06 MB + 4 MB + a few hundred bytes per device.
+static __device__ __align__(256) float4 g_scratch_G[kNoallocGElems];
+static __device__ __align__(256) float4 g_scratch_Z[kNoallocMaxFft];
+static __device__ __align__(256) SkyConst g_scratch_sky;
+static __device__ __align__(256) TmplCoef g_scratch_coef;
+
+constexpr int kMaxDevices = 64;
+struct DevPtrs {
+  float4* G;
+  float4* Z;
+  SkyConst* sky;
+  TmplCoef* coef;
+};
+std::mutex g_setup_mutex;
+DevPtrs g_ptrs[kMaxDevices];
+std::atomic<bool> g_ready[kMaxDevices];
+
+// Device addresses of the scratch arrays on the current device (host code
+// sees only host-side stand-ins for the symbols).
+int device_ptrs(DevPtrs* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FSTAT_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return FSTAT_ERR_UNSUPPORTED;
+  if (!g_ready[dev].load(std::memory_order_acquire)) {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_ready[dev].load(std::memory_order_relaxed)) {
+      DevPtrs p{};
+      if (cudaGetSymbolAddress((void**)&p.G, g_scratch_G) != cudaSuccess) return FSTAT_ERR_CUDA;
+      if (cudaGetSymbolAddress((void**)&p.Z, g_scratch_Z) != cudaSuccess) return FSTAT_ERR_CUDA;
+      if (cudaGetSymbolAddress((void**)&p.sky, g_scratch_sky) != cudaSuccess) return FSTAT_ERR_CUDA;
+      if (cudaGetSymbolAddress((void**)&p.coef, g_scratch_coef) != cudaSuccess) return FSTAT_ERR_CUDA;
+      g_ptrs[dev] = p;
+      g_ready[dev].store(true, std::memory_order_release);
+    }
+  }
+  *out = g_ptrs[dev];
+  return FSTAT_OK;
+}
+
+// Per-call constants: 2F weights from A, B, C and the spindown polynomial
+// phi(s) = p0 + p1 s + p2 s^2 + p3 s^3 (cycles), s = j - J, for
+// tau = tau0 + j dt = (j - j_ref) dt with j_ref = -tau0 / dt.
+__global__ void k_noalloc_setup(double A, double B, double C, double tau0, double dt, double f1dot,
+                                double f2dot) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double D = A * B - C * C;
+  g_scratch_sky.A = A;
+  g_scratch_sky.B = B;
+  g_scratch_sky.C = C;
+  g_scratch_sky.D = D;
+  g_scratch_sky.kA = 2.0 * A / D;
+  g_scratch_sky.kB = 2.0 * B / D;
+  g_scratch_sky.kC = 4.0 * C / D;
+  g_scratch_sky.kAf = (float)g_scratch_sky.kA;
+  g_scratch_sky.kBf = (float)g_scratch_sky.kB;
+  g_scratch_sky.kCf = (float)g_scratch_sky.kC;
+  double jr = -tau0 / dt;
+  double J = rint(jr);
+  double e = jr - J;
+  double c2 = f1dot * dt * dt / 2.0;
+  double c3 = f2dot * dt * dt * dt / 6.0;
+  TmplCoef c;
+  c.p[3] = c3;
+  c.p[2] = c2 - 3.0 * c3 * e;
+  c.p[1] = -2.0 * c2 * e + 3.0 * c3 * e * e;
+  c.p[0] = c2 * e * e - c3 * e * e * e;
+  for (int q = 0; q < 4; ++q) {
+    float h = (float)c.p[q];
+    c.hi[q] = h;
+    c.lo[q] = (float)(c.p[q] - (double)h);
+  }
+  c.J = (int)J;
+  c.pad_ = 0;
+  g_scratch_coef = c;
+}
+
+// natural order j -> column-major [(j mod n1) * lc + j / n1]
+__global__ void k_noalloc_columns(const float4* __restrict__ g, int64_t n, int n1, int64_t lc,
+                                  float4* __restrict__ out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    out[(j % n1) * lc + j / n1] = g[j];
+}
+
+}  // namespace
+}  // namespace fstat
+
+using namespace fstat;
+
+extern "C" int fstat_twoF_noalloc(const void* g_pairs, int64_t n_samples, int64_t n_fft, double dt,
+                                  double tau0, double A, double B, double C, double f1dot,
+                                  double f2dot, float* twoF, void* stream) {
+  if (!g_pairs || !twoF || n_samples < 1 || !(dt > 0.0) || !isfinite(tau0) || !isfinite(f1dot) ||
+      !isfinite(f2dot) || !isfinite(A) || !isfinite(B) || !isfinite(C))
+    return FSTAT_ERR_INVALID_ARG;
+  if (n_fft <= 0 || (n_fft & (n_fft - 1))) return FSTAT_ERR_INVALID_ARG;
+  int log2n = 0;
+  while ((int64_t(1) << log2n) < n_fft) ++log2n;
+  if (n_fft > kNoallocMaxFft || log2n < 2 * kMinLog2) return FSTAT_ERR_UNSUPPORTED;
+  if (n_samples > n_fft) return FSTAT_ERR_INVALID_ARG;
+  double D = A * B - C * C;
+  if (!(D > 1e-12 * A * B) || !(A > 0.0) || !(B > 0.0)) return FSTAT_ERR_DEGENERATE;
+
+  DevPtrs p;
+  int rc = device_ptrs(&p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int log2n1 = log2n / 2, log2n2 = log2n - log2n1;
+  const int n1 = 1 << log2n1, n2 = 1 << log2n2;
+  const int64_t lc = (n_samples + n1 - 1) / n1;
+
+  k_noalloc_setup<<<1, 32, 0, st>>>(A, B, C, tau0, dt, f1dot, f2dot);
+  int blocks = (int)((n_samples + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_noalloc_columns<<<blocks, 256, 0, st>>>((const float4*)g_pairs, n_samples, n1, lc, p.G);
+  if (cudaGetLastError() != cudaSuccess) return FSTAT_ERR_CUDA;
+  cudaError_t e = launch_pass_a_f32(log2n2, p.G, lc, n_samples, n1, log2n, p.coef, p.Z, st);
+  if (e != cudaSuccess) return FSTAT_ERR_CUDA;
+  e = launch_pass_b_f32(log2n1, p.Z, n2, p.sky, twoF, st);
+  if (e != cudaSuccess) return FSTAT_ERR_CUDA;
+  return FSTAT_OK;
+}
