@@ -153,6 +153,22 @@ int fstat_kernel_stats(fstat_plan* plan, int kernel, int64_t* launches, double* 
 int fstat_get_split(const fstat_plan* plan, int64_t* n1, int64_t* n2);
 int fstat_set_split(fstat_plan* plan, int64_t n1);
 
+/* Launch shapes of the two FFT passes: columns per CTA of pass A (ca),
+ * rows per CTA of pass B (cb), 0 = default for the length; radix schedule
+ * va / vb: 0 = radix-16 first, 1 = radix-8 first (lengths >= 1024).  A
+ * shape that is not compiled for the current split makes fstat_compute
+ * return FSTAT_ERR_CUDA. */
+int fstat_get_cta(const fstat_plan* plan, int* ca, int* va, int* cb, int* vb);
+int fstat_set_cta(fstat_plan* plan, int ca, int va, int cb, int vb);
+
+/* Autotuner: times every compiled (split, ca, va, cb, vb) for this plan's n_fft on
+ * the current data with CUDA events on `stream` and keeps the fastest.
+ * Results are cached per (GPU name, n_samples, n_fft, precision, n_det) in
+ * the process and, if the environment variable FSTAT_AUTOTUNE_CACHE names
+ * a file, in that file.  Synchronises; invalidates cached per-sky work.
+ * Errors: NOT_READY (no data), OOM, CUDA. */
+int fstat_autotune(fstat_plan* plan, void* stream);
+
 /* 2F for one template from a caller-supplied resampled series, allocating
  * nothing.  The paper has no counterpart: this exists for callers that may
  * not call cudaMalloc (a plug-in inside an application whose memory pool

@@ -41,7 +41,7 @@ EXPORTS = (
     "fstat_plan_create", "fstat_set_data", "fstat_compute", "fstat_freq_axis",
     "fstat_invalidate_sky", "fstat_export_sky", "fstat_sync", "fstat_set_profiling",
     "fstat_kernel_stats", "fstat_get_split", "fstat_set_split", "fstat_plan_destroy",
-    "fstat_strerror", "fstat_twoF_noalloc",
+    "fstat_strerror", "fstat_twoF_noalloc", "fstat_get_cta", "fstat_set_cta", "fstat_autotune",
 )
 
 
@@ -110,6 +110,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fstat_plan_destroy": (None, [P]),
         "fstat_strerror": (ctypes.c_char_p, [i32]),
         "fstat_twoF_noalloc": (i32, [P, i64, i64, dbl, dbl, dbl, dbl, dbl, dbl, dbl, P, P]),
+        "fstat_get_cta": (i32, [P] + [ctypes.POINTER(i32)] * 4),
+        "fstat_set_cta": (i32, [P, i32, i32, i32, i32]),
+        "fstat_autotune": (i32, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -290,3 +293,17 @@ class FstatPlan:
 
     def set_split(self, n1: int):
         _check(self._lib.fstat_set_split(self._p, int(n1)), "fstat_set_split")
+
+    @property
+    def cta(self):
+        """(ca, va, cb, vb): pass-A columns/CTA and radix schedule, pass-B rows/CTA and schedule."""
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(self._lib.fstat_get_cta(self._p, *[ctypes.byref(x) for x in v]), "fstat_get_cta")
+        return tuple(x.value for x in v)
+
+    def set_cta(self, ca: int, cb: int, va: int = 0, vb: int = 0):
+        _check(self._lib.fstat_set_cta(self._p, int(ca), int(va), int(cb), int(vb)), "fstat_set_cta")
+
+    def autotune(self, stream=None):
+        """fstat_autotune: pick the fastest FFT split and CTA shapes."""
+        _check(self._lib.fstat_autotune(self._p, _stream_handle(stream)), "fstat_autotune")

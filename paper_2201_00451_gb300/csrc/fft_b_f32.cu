@@ -1,0 +1,11 @@
+// FP32 (mixed-precision path) instantiations of FFT pass B.
+#include "fft_impl.cuh"
+
+namespace fstat {
+
+cudaError_t launch_pass_b_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
+                              const SkyConst* sky, float* out, cudaStream_t st) {
+  return fft::dispatch_b<float>(log2_n1, cb, vb, Z, n2, twB, sky, out, st);
+}
+
+}  // namespace fstat

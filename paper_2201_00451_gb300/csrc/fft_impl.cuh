@@ -12,7 +12,13 @@
 // registers).  Pass A computes the spindown phase on the fly, pass B
 // evaluates eq. (Fstat) on the final butterfly outputs and stores 2F in
 // ascending frequency (fftshift folded into the index).  Fa and Fb travel
-// together as one 16-byte (FP32) / 32-byte (FP64) element.
+// together as one 16-byte (FP32) / 32-byte (FP64) element, so every index,
+// twiddle and phase is computed once for both.
+//
+// Twiddles are computed per butterfly: one sine/cosine of the reduced angle
+// (hardware sine/cosine in FP32, sincospi in FP64) and powers by binary
+// splitting.  CA / CB, the columns / rows per CTA, are template parameters
+// chosen per FFT length by the autotuner.
 #pragma once
 
 #include "fstat_internal.cuh"
@@ -20,10 +26,27 @@
 namespace fstat {
 namespace fft {
 
+#ifndef FSTAT_PASSB_TABLE
+#define FSTAT_PASSB_TABLE 0
+#endif
+// Stockham twiddles are computed (hardware sine/cosine of the reduced angle
+// and powers) in both passes; the table variant of pass B (build with
+// -DFSTAT_PASSB_TABLE=1) measured 11% slower on GB300 at n_fft = 2^22.
+constexpr bool kPassBTable = FSTAT_PASSB_TABLE != 0;
+
+template <typename T> struct TwT;
+template <> struct TwT<float> { using type = float2; };
+template <> struct TwT<double> { using type = double2; };
+
 // ------------------------------------------------------------ radix schedule
-__host__ __device__ constexpr int np_of(int L) { return L <= 256 ? 2 : 3; }
-__host__ __device__ constexpr int r_of(int L, int p) {
-  return L == 32    ? (p == 0 ? 8 : 4)
+// V = 0: radix-16 first (fewest shared-memory passes, 16 points per thread);
+// V = 1 (lengths >= 1024): radix-8 first (8 points per thread, half the
+// registers, one more pass).  The first radix is the largest.
+__host__ __device__ constexpr bool r8(int L, int V) { return V == 1 && L >= 1024; }
+__host__ __device__ constexpr int np_of(int L, int V) { return r8(L, V) ? 4 : (L <= 256 ? 2 : 3); }
+__host__ __device__ constexpr int r_of(int L, int p, int V) {
+  return r8(L, V)   ? (p < 3 ? 8 : L / 512)
+       : L == 32    ? (p == 0 ? 8 : 4)
        : L == 64    ? 8
        : L == 128   ? (p == 0 ? 16 : 8)
        : L == 256   ? 16
@@ -32,26 +55,60 @@ __host__ __device__ constexpr int r_of(int L, int p) {
        : L == 2048  ? (p == 2 ? 8 : 16)
        : 16;  // 4096
 }
-__host__ __device__ constexpr int ns_of(int L, int p) { return p == 0 ? 1 : ns_of(L, p - 1) * r_of(L, p - 1); }
+__host__ __device__ constexpr int ns_of(int L, int p, int V) {
+  return p == 0 ? 1 : ns_of(L, p - 1, V) * r_of(L, p - 1, V);
+}
 __host__ __device__ constexpr int log2c(int x) { return x <= 1 ? 0 : 1 + log2c(x / 2); }
 
-template <typename T, int L> struct Shape {
-  static constexpr int NP = np_of(L);
-  static constexpr int R0 = r_of(L, 0);           // largest radix, points per thread
+template <typename T, int L, int V = 0> struct Shape {
+  static constexpr int NP = np_of(L, V);
+  static constexpr int R0 = r_of(L, 0, V);        // largest radix, points per thread
   static constexpr int TPC = L / R0;              // threads per column
   static constexpr int PS = log2c(R0);            // shared-memory padding shift
   static constexpr int LP = L + (L >> PS);        // padded column length
-  static constexpr int RL = r_of(L, NP - 1);      // last radix
+  static constexpr int RL = r_of(L, NP - 1, V);   // last radix
   static constexpr int NSL = L / RL;              // span of the last pass
-  static constexpr int CA = TPC >= 128 ? 1 : 128 / TPC;                       // columns / CTA (A)
-  static constexpr int CB0 = sizeof(T) == 4 ? 2 : 1;
-  static constexpr int CB = TPC >= 128 ? CB0 : (128 / TPC > CB0 ? 128 / TPC : CB0);  // rows / CTA (B)
+  static constexpr int CA_DEF = TPC >= 128 ? 1 : 128 / TPC;
+  static constexpr int CB_MIN = sizeof(T) == 4 ? 2 : 1;
+  static constexpr int CB_DEF = TPC >= 128 ? CB_MIN : (128 / TPC > CB_MIN ? 128 / TPC : CB_MIN);
   using PM = typename PairMem<T>::type;
-  static constexpr size_t SMEM_A = (size_t)CA * LP * sizeof(PM);
-  static constexpr size_t SMEM_B = (size_t)CB * LP * sizeof(PM);
+  using TW = typename TwT<T>::type;
 };
 
+template <typename T, int L, int C, int V = 0> constexpr bool cfg_ok() {
+  using S = Shape<T, L, V>;
+  return C * S::TPC >= 32 && C * S::TPC <= 1024 &&
+         (size_t)C * S::LP * sizeof(typename S::PM) <= (size_t)200 * 1024;
+}
+
 __device__ __forceinline__ int pad_idx(int pos, int ps) { return pos + (pos >> ps); }
+
+template <typename TW> __device__ __forceinline__ TW tw_ld(const TW* p) { return __ldg(p); }
+
+// (cos, sin) of 2 pi x for x in turns.  FP32: reduce x to [-1/2, 1/2] (exact)
+// and use the hardware sine/cosine, accurate to ~4e-7 absolute on [-pi, pi];
+// FP64: sincospi.
+__device__ __forceinline__ void turn_sincos(float x, float* s, float* c) {
+  const float r = x - rintf(x);
+  __sincosf(6.28318530717958647692f * r, s, c);
+}
+__device__ __forceinline__ void turn_sincos(double x, double* s, double* c) {
+  sincospi(2.0 * x, s, c);
+}
+
+// wc[q] + i ws[q] = (c + i s)^q for q = 0..R-1 by binary splitting (the
+// error grows with log2 q, not q).
+template <typename T, int R>
+__device__ __forceinline__ void powers(T c, T s, T* wc, T* ws) {
+  wc[0] = (T)1; ws[0] = (T)0;
+  wc[1] = c; ws[1] = s;
+#pragma unroll
+  for (int q = 2; q < R; ++q) {
+    const int h = q / 2, l = q - h;
+    wc[q] = wc[h] * wc[l] - ws[h] * ws[l];
+    ws[q] = wc[h] * ws[l] + ws[h] * wc[l];
+  }
+}
 
 // ------------------------------------------------------------- small DFTs
 template <typename T> __device__ __forceinline__ Pair<T> w8_1(const Pair<T>& x) {  // * (1 - i)/sqrt2
@@ -110,33 +167,19 @@ template <typename T, int R> __device__ __forceinline__ void dft(Pair<T>* x) {
   else dft16(x);
 }
 
-// x[q] *= w^q for q = 1..R-1, w = (c + i s); powers by binary splitting
-// (error grows with log2 q, not q).
-template <typename T, int R> __device__ __forceinline__ void twiddle(Pair<T>* x, T c, T s) {
-  T wc[R], ws[R];
-  wc[0] = (T)1; ws[0] = (T)0;
-  wc[1] = c; ws[1] = s;
-#pragma unroll
-  for (int q = 2; q < R; ++q) {
-    const int h = q / 2, l = q - h;
-    wc[q] = wc[h] * wc[l] - ws[h] * ws[l];
-    ws[q] = wc[h] * ws[l] + ws[h] * wc[l];
-  }
-#pragma unroll
-  for (int q = 1; q < R; ++q) x[q] = pmul(x[q], wc[q], ws[q]);
-}
-
 // --------------------------------------------------------- Stockham passes
 // After pass 0 (done by the caller, in registers), store it and run passes
 // 1..NP-1.  On return v holds the last pass's outputs: butterfly
 // b = t + q * TPC, output index b + s * NSL in v[q * RL + s].
 // Shared-memory address of logical position pos is pad(pos) * STRIDE.
-template <typename T, int L, int STRIDE, int P>
-__device__ __forceinline__ void passes(Pair<T>* v, typename PairMem<T>::type* buf, int t) {
-  using S = Shape<T, L>;
-  constexpr int R = r_of(L, P);
-  constexpr int NS = ns_of(L, P);
+template <typename T, int L, int V, int STRIDE, int P, bool TABLE>
+__device__ __forceinline__ void passes(Pair<T>* v, typename PairMem<T>::type* buf, int t,
+                                       const typename TwT<T>::type* __restrict__ twL) {
+  using S = Shape<T, L, V>;
+  constexpr int R = r_of(L, P, V);
+  constexpr int NS = ns_of(L, P, V);
   constexpr int NB = S::R0 / R;  // butterflies per thread
+  constexpr int STEP = L / (NS * R);
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int b = t + q * S::TPC;
@@ -147,11 +190,19 @@ __device__ __forceinline__ void passes(Pair<T>* v, typename PairMem<T>::type* bu
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int b = t + q * S::TPC;
-    const int k = b & (NS - 1);
-    if (NS > 1) {
-      T sn, cs;
-      sincospi_t((T)(-2 * k) / (T)(NS * R), &sn, &cs);
-      twiddle<T, R>(v + q * R, cs, sn);
+    if constexpr (TABLE) {
+      const int k = (b & (NS - 1)) * STEP;
+#pragma unroll
+      for (int s = 1; s < R; ++s) {
+        const auto w = tw_ld(twL + k * s);
+        v[q * R + s] = pmul(v[q * R + s], (T)w.x, (T)w.y);
+      }
+    } else if (NS > 1) {
+      T sn, cs, wc[R], ws[R];
+      turn_sincos(-(T)(b & (NS - 1)) / (T)(NS * R), &sn, &cs);
+      powers<T, R>(cs, sn, wc, ws);
+#pragma unroll
+      for (int s = 1; s < R; ++s) v[q * R + s] = pmul(v[q * R + s], wc[s], ws[s]);
     }
     dft<T, R>(v + q * R);
   }
@@ -164,14 +215,14 @@ __device__ __forceinline__ void passes(Pair<T>* v, typename PairMem<T>::type* bu
       for (int s = 0; s < R; ++s) pstore(buf + pad_idx(base + s * NS, S::PS) * STRIDE, v[q * R + s]);
     }
     __syncthreads();
-    passes<T, L, STRIDE, P + 1>(v, buf, t);
+    passes<T, L, V, STRIDE, P + 1, TABLE>(v, buf, t, twL);
   }
 }
 
 // store pass-0 outputs (one radix-R0 butterfly per thread, Ns = 1)
-template <typename T, int L, int STRIDE>
+template <typename T, int L, int V, int STRIDE>
 __device__ __forceinline__ void store_pass0(const Pair<T>* v, typename PairMem<T>::type* buf, int t) {
-  using S = Shape<T, L>;
+  using S = Shape<T, L, V>;
 #pragma unroll
   for (int s = 0; s < S::R0; ++s) pstore(buf + pad_idx(t * S::R0 + s, S::PS) * STRIDE, v[s]);
   __syncthreads();
@@ -180,7 +231,9 @@ __device__ __forceinline__ void store_pass0(const Pair<T>* v, typename PairMem<T
 // ----------------------------------------------------- spindown phase
 // e^{-i 2 pi phi(s)}, phi = ((p3 s + p2) s + p1) s + p0 cycles, s exact in FP32.
 // FP32 path: Horner in double-float (error-free products and sums with
-// explicitly rounded operations so the compiler cannot contract them).
+// explicitly rounded operations so the compiler cannot contract them), mod
+// 1 in double-float, then the rotation of the reduced phase f in [-1/2, 1/2]
+// (|2 pi f| <= pi, where the hardware sine/cosine is accurate to ~4e-7).
 __device__ __forceinline__ void spin_rot(const TmplCoef& c, int si, float* cs, float* sn) {
   const float s = (float)si;
   float h = c.hi[3], l = c.lo[3];
@@ -199,7 +252,7 @@ __device__ __forceinline__ void spin_rot(const TmplCoef& c, int si, float* cs, f
   const float k = rintf(h);
   const float f = __fadd_rn(__fsub_rn(h, k), l);
   float sv, cv;
-  sincospif(2.0f * f, &sv, &cv);
+  __sincosf(6.28318530717958647692f * f, &sv, &cv);
   *cs = cv;
   *sn = -sv;
 }
@@ -214,17 +267,19 @@ __device__ __forceinline__ void spin_rot(const TmplCoef& c, int si, double* cs, 
 }
 
 // ------------------------------------------------------------- pass A
-template <typename T, int L>
-__global__ void __launch_bounds__(Shape<T, L>::CA * Shape<T, L>::TPC)
-k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int n1, int log2N,
-         const TmplCoef* __restrict__ coefp, typename PairMem<T>::type* __restrict__ Z) {
-  using S = Shape<T, L>;
+template <typename T, int L, int CA, int V>
+__global__ void __launch_bounds__(CA * Shape<T, L, V>::TPC)
+k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int n1,
+         const typename TwT<T>::type* __restrict__ twL, const typename TwT<T>::type* __restrict__ tw_hi,
+         const typename TwT<T>::type* __restrict__ tw_lo, int h, const TmplCoef* __restrict__ coefp,
+         typename PairMem<T>::type* __restrict__ Z) {
+  using S = Shape<T, L, V>;
   using PM = typename PairMem<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PM* smem = reinterpret_cast<PM*>(smem_raw);
   const int c = threadIdx.x / S::TPC;
   const int t = threadIdx.x % S::TPC;
-  const int col = blockIdx.x * S::CA + c;
+  const int col = blockIdx.x * CA + c;
   PM* buf = smem + c * S::LP;
   const TmplCoef tc = *coefp;
   const PM* gcol = G + (int64_t)col * lc;
@@ -244,48 +299,55 @@ k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int
     }
   }
   dft<T, S::R0>(v);
-  store_pass0<T, L, 1>(v, buf, t);
-  passes<T, L, 1, 1>(v, buf, t);
+  store_pass0<T, L, V, 1>(v, buf, t);
+  passes<T, L, V, 1, 1, false>(v, buf, t, twL);
 
-  // four-step twiddle W_N^{col k2}, k2 = b + s * NSL, and store Z[col][k2]
-  const T scale = (T)2 / (T)(1 << log2N);
+  // four-step twiddle W_N^{col k2} = W_N^{col b} (W_N^{col NSL})^s for
+  // k2 = b + s * NSL, and store Z[col][k2]
+  const int log2N = log2c(L) + 31 - __clz(n1);
+  const T inv_n = (T)1 / (T)(1 << log2N);
+  T sc, ss, stc[S::RL], sts[S::RL];
+  turn_sincos(-(T)(col * S::NSL) * inv_n, &ss, &sc);
+  powers<T, S::RL>(sc, ss, stc, sts);
   PM* zrow = Z + (int64_t)col * L;
   constexpr int NB = S::R0 / S::RL;
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int b = t + q * S::TPC;
-    T s0, c0, s1, c1;
-    sincospi_t(-(T)(col * b) * scale, &s0, &c0);
-    sincospi_t(-(T)(col * S::NSL) * scale, &s1, &c1);
+    T bc, bs;
+    turn_sincos(-(T)(col * b) * inv_n, &bs, &bc);
     Pair<T>* x = v + q * S::RL;
 #pragma unroll
-    for (int s = 0; s < S::RL; ++s) x[s] = pmul(x[s], c0, s0);
-    twiddle<T, S::RL>(x, c1, s1);
-#pragma unroll
-    for (int s = 0; s < S::RL; ++s) pstore(zrow + b + s * S::NSL, x[s]);
+    for (int s = 0; s < S::RL; ++s) {
+      const T wc = bc * stc[s] - bs * sts[s];
+      const T ws = bc * sts[s] + bs * stc[s];
+      pstore(zrow + b + s * S::NSL, pmul(x[s], wc, ws));
+    }
   }
+  (void)tw_hi; (void)tw_lo; (void)h;
 }
 
 // ------------------------------------------------------------- pass B
-template <typename T, int L>
-__global__ void __launch_bounds__(Shape<T, L>::CB * Shape<T, L>::TPC)
-k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2, const SkyConst* __restrict__ sky,
+template <typename T, int L, int CB, int V>
+__global__ void __launch_bounds__(CB * Shape<T, L, V>::TPC)
+k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
+         const typename TwT<T>::type* __restrict__ twL, const SkyConst* __restrict__ sky,
          float* __restrict__ out) {
-  using S = Shape<T, L>;
+  using S = Shape<T, L, V>;
   using PM = typename PairMem<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PM* smem = reinterpret_cast<PM*>(smem_raw);
-  const int c = threadIdx.x % S::CB;
-  const int t = threadIdx.x / S::CB;
-  const int k2 = blockIdx.x * S::CB + c;
+  const int c = threadIdx.x % CB;
+  const int t = threadIdx.x / CB;
+  const int k2 = blockIdx.x * CB + c;
   PM* buf = smem + c;
 
   Pair<T> v[S::R0];
 #pragma unroll
   for (int s = 0; s < S::R0; ++s) v[s] = pload_g(Z + (int64_t)(t + s * S::TPC) * n2 + k2);
   dft<T, S::R0>(v);
-  store_pass0<T, L, S::CB>(v, buf, t);
-  passes<T, L, S::CB, 1>(v, buf, t);
+  store_pass0<T, L, V, CB>(v, buf, t);
+  passes<T, L, V, CB, 1, kPassBTable && sizeof(T) == 4>(v, buf, t, twL);
 
   T kA, kB, kC;
   if constexpr (sizeof(T) == 4) { kA = sky->kAf; kB = sky->kBf; kC = sky->kCf; }
@@ -303,71 +365,135 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2, const SkyConst
       T re = x.ar * x.br + x.ai * x.bi;
       T tf = kB * fa2 + kA * fb2 - kC * re;
       const int m = k2 + n2 * ((k1 + L / 2) & (L - 1));
-      out[m] = (float)tf;
+      __stcs(out + m, (float)tf);  // streaming store: keep G and Z in L2
     }
   }
 }
 
-template <typename T, int L>
-cudaError_t run_a(const void* G, int64_t lc, int64_t n, int n1, int log2N, const TmplCoef* coef,
-                  void* Z, cudaStream_t st) {
-  using S = Shape<T, L>;
+// ------------------------------------------------------------- launchers
+template <typename T, int L, int CA, int V>
+cudaError_t run_a(const void* G, int64_t lc, int64_t n, int n1, const void* twA, const void* hi,
+                  const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st) {
+  using S = Shape<T, L, V>;
+  constexpr size_t smem = (size_t)CA * S::LP * sizeof(typename S::PM);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_pass_a<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::SMEM_A);
+    cudaError_t e = cudaFuncSetAttribute(k_pass_a<T, L, CA, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_pass_a<T, L><<<n1 / S::CA, S::CA * S::TPC, S::SMEM_A, st>>>(
-      (const typename S::PM*)G, lc, (int)n, n1, log2N, coef, (typename S::PM*)Z);
+  if (n1 % CA) return cudaErrorInvalidConfiguration;
+  using TW = typename S::TW;
+  k_pass_a<T, L, CA, V><<<n1 / CA, CA * S::TPC, smem, st>>>(
+      (const typename S::PM*)G, lc, (int)n, n1, (const TW*)twA, (const TW*)hi, (const TW*)lo, h, coef,
+      (typename S::PM*)Z);
   return cudaGetLastError();
 }
 
-template <typename T, int L>
-cudaError_t run_b(const void* Z, int n2, const SkyConst* sky, float* out, cudaStream_t st) {
-  using S = Shape<T, L>;
+template <typename T, int L, int CB, int V>
+cudaError_t run_b(const void* Z, int n2, const void* twB, const SkyConst* sky, float* out, cudaStream_t st) {
+  using S = Shape<T, L, V>;
+  constexpr size_t smem = (size_t)CB * S::LP * sizeof(typename S::PM);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_pass_b<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::SMEM_B);
+    cudaError_t e = cudaFuncSetAttribute(k_pass_b<T, L, CB, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_pass_b<T, L><<<n2 / S::CB, S::CB * S::TPC, S::SMEM_B, st>>>((const typename S::PM*)Z, n2, sky, out);
+  if (n2 % CB) return cudaErrorInvalidConfiguration;
+  k_pass_b<T, L, CB, V><<<n2 / CB, CB * S::TPC, smem, st>>>(
+      (const typename S::PM*)Z, n2, (const typename S::TW*)twB, sky, out);
   return cudaGetLastError();
 }
+
+// CTA shapes compiled per length: the default plus wider ones and the
+// radix-8 schedule, only for the lengths the configured workloads use
+// (512..4096) and only in FP32.
+template <int L> constexpr bool wide_variants() { return L >= 512; }
+
+// shape code: c = columns (A) / rows (B) per CTA, 0 = default; v = schedule
+template <typename T, int L, int V>
+cudaError_t pick_a_v(int ca, const void* G, int64_t lc, int64_t n, int n1, const void* twA, const void* hi,
+                     const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st) {
+  switch (ca) {
+    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_a<T, L, 1, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st); break;
+    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_a<T, L, 2, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st); break;
+    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_a<T, L, 4, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st); break;
+    default: break;
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+template <typename T, int L>
+cudaError_t pick_a(int ca, int v, const void* G, int64_t lc, int64_t n, int n1, const void* twA, const void* hi,
+                   const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st) {
+  using S = Shape<T, L, 0>;
+  if (ca <= 0) ca = S::CA_DEF;
+  if (v == 0 && ca == S::CA_DEF) return run_a<T, L, S::CA_DEF, 0>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st);
+  if constexpr (sizeof(T) == 4 && wide_variants<L>()) {
+    if (v == 0) return pick_a_v<T, L, 0>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st);
+    if constexpr (L >= 1024)
+      if (v == 1) return pick_a_v<T, L, 1>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st);
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+template <typename T, int L, int V>
+cudaError_t pick_b_v(int cb, const void* Z, int n2, const void* twB, const SkyConst* sky, float* out,
+                     cudaStream_t st) {
+  switch (cb) {
+    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_b<T, L, 1, V>(Z, n2, twB, sky, out, st); break;
+    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_b<T, L, 2, V>(Z, n2, twB, sky, out, st); break;
+    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_b<T, L, 4, V>(Z, n2, twB, sky, out, st); break;
+    case 8: if constexpr (cfg_ok<T, L, 8, V>()) return run_b<T, L, 8, V>(Z, n2, twB, sky, out, st); break;
+    default: break;
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+template <typename T, int L>
+cudaError_t pick_b(int cb, int v, const void* Z, int n2, const void* twB, const SkyConst* sky, float* out,
+                   cudaStream_t st) {
+  using S = Shape<T, L, 0>;
+  if (cb <= 0) cb = S::CB_DEF;
+  if (v == 0 && cb == S::CB_DEF) return run_b<T, L, S::CB_DEF, 0>(Z, n2, twB, sky, out, st);
+  if constexpr (sizeof(T) == 4 && wide_variants<L>()) {
+    if (v == 0) return pick_b_v<T, L, 0>(cb, Z, n2, twB, sky, out, st);
+    if constexpr (L >= 1024)
+      if (v == 1) return pick_b_v<T, L, 1>(cb, Z, n2, twB, sky, out, st);
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+#define FSTAT_LEN_CASES(F, ...)            \
+  case 5: return F<T, 32>(__VA_ARGS__);    \
+  case 6: return F<T, 64>(__VA_ARGS__);    \
+  case 7: return F<T, 128>(__VA_ARGS__);   \
+  case 8: return F<T, 256>(__VA_ARGS__);   \
+  case 9: return F<T, 512>(__VA_ARGS__);   \
+  case 10: return F<T, 1024>(__VA_ARGS__); \
+  case 11: return F<T, 2048>(__VA_ARGS__); \
+  case 12: return F<T, 4096>(__VA_ARGS__);
 
 template <typename T>
-cudaError_t dispatch_a(int log2_n2, const void* G, int64_t lc, int64_t n, int n1, int log2N,
-                       const TmplCoef* coef, void* Z, cudaStream_t st) {
+cudaError_t dispatch_a(int log2_n2, int ca, int v, const void* G, int64_t lc, int64_t n, int n1, const void* twA,
+                       const void* hi, const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st) {
   switch (log2_n2) {
-    case 5: return run_a<T, 32>(G, lc, n, n1, log2N, coef, Z, st);
-    case 6: return run_a<T, 64>(G, lc, n, n1, log2N, coef, Z, st);
-    case 7: return run_a<T, 128>(G, lc, n, n1, log2N, coef, Z, st);
-    case 8: return run_a<T, 256>(G, lc, n, n1, log2N, coef, Z, st);
-    case 9: return run_a<T, 512>(G, lc, n, n1, log2N, coef, Z, st);
-    case 10: return run_a<T, 1024>(G, lc, n, n1, log2N, coef, Z, st);
-    case 11: return run_a<T, 2048>(G, lc, n, n1, log2N, coef, Z, st);
-    case 12: return run_a<T, 4096>(G, lc, n, n1, log2N, coef, Z, st);
+    FSTAT_LEN_CASES(pick_a, ca, v, G, lc, n, n1, twA, hi, lo, h, coef, Z, st)
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename T>
-cudaError_t dispatch_b(int log2_n1, const void* Z, int n2, const SkyConst* sky, float* out, cudaStream_t st) {
+cudaError_t dispatch_b(int log2_n1, int cb, int v, const void* Z, int n2, const void* twB, const SkyConst* sky,
+                       float* out, cudaStream_t st) {
   switch (log2_n1) {
-    case 5: return run_b<T, 32>(Z, n2, sky, out, st);
-    case 6: return run_b<T, 64>(Z, n2, sky, out, st);
-    case 7: return run_b<T, 128>(Z, n2, sky, out, st);
-    case 8: return run_b<T, 256>(Z, n2, sky, out, st);
-    case 9: return run_b<T, 512>(Z, n2, sky, out, st);
-    case 10: return run_b<T, 1024>(Z, n2, sky, out, st);
-    case 11: return run_b<T, 2048>(Z, n2, sky, out, st);
-    case 12: return run_b<T, 4096>(Z, n2, sky, out, st);
+    FSTAT_LEN_CASES(pick_b, cb, v, Z, n2, twB, sky, out, st)
     default: return cudaErrorInvalidValue;
   }
 }
+
+#undef FSTAT_LEN_CASES
 
 }  // namespace fft
 }  // namespace fstat

@@ -105,13 +105,29 @@ void launch_sky(const Geo& g, int precision, double alpha, double delta, const v
 void launch_tmpl_coef(const SkyConst* sky, double dt, const fstat_template* tmpl,
                       const int* order, int first, int count, TmplCoef* out, cudaStream_t st);
 void launch_check_finite(const void* x, int dtype, int64_t n, int* err, cudaStream_t st);
-cudaError_t launch_pass_a_f32(int log2_n2, const void* G, int64_t lc, int64_t n, int n1, int log2N,
-                              const TmplCoef* coef, void* Z, cudaStream_t st);
-cudaError_t launch_pass_b_f32(int log2_n1, const void* Z, int n2, const SkyConst* sky, float* out,
-                              cudaStream_t st);
-cudaError_t launch_pass_a_f64(int log2_n2, const void* G, int64_t lc, int64_t n, int n1, int log2N,
-                              const TmplCoef* coef, void* Z, cudaStream_t st);
-cudaError_t launch_pass_b_f64(int log2_n1, const void* Z, int n2, const SkyConst* sky, float* out,
-                              cudaStream_t st);
+// Twiddle tables (tables.cu): pointers into one device block.
+struct TwiddleTables {
+  const void* a;   // pass A Stockham roots, N2 entries
+  const void* b;   // pass B Stockham roots, N1 entries
+  const void* lo;  // W_N^i, i < 2^h
+  const void* hi;  // W_N^(i 2^h)
+  int h;
+  size_t bytes;
+};
+TwiddleTables twiddle_layout(int precision, int log2n1, int log2n2, void* base);
+cudaError_t build_twiddles(int precision, int log2n1, int log2n2, void* base, cudaStream_t st);
+
+// FFT passes; ca / cb = columns / rows per CTA (0 = default for the length),
+// va / vb = radix schedule (0 = radix-16 first, 1 = radix-8 first).
+cudaError_t launch_pass_a_f32(int log2_n2, int ca, int va, const void* G, int64_t lc, int64_t n, int n1,
+                              const void* twA, const void* hi, const void* lo, int h, const TmplCoef* coef,
+                              void* Z, cudaStream_t st);
+cudaError_t launch_pass_b_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
+                              const SkyConst* sky, float* out, cudaStream_t st);
+cudaError_t launch_pass_a_f64(int log2_n2, int ca, int va, const void* G, int64_t lc, int64_t n, int n1,
+                              const void* twA, const void* hi, const void* lo, int h, const TmplCoef* coef,
+                              void* Z, cudaStream_t st);
+cudaError_t launch_pass_b_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
+                              const SkyConst* sky, float* out, cudaStream_t st);
 
 }  // namespace fstat

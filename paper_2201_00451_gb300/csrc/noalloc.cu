@@ -26,10 +26,11 @@ constexpr int kNoallocMaxLog2 = 18;  // n_fft <= 2^18
 constexpr int64_t kNoallocMaxFft = int64_t(1) << kNoallocMaxLog2;
 constexpr int64_t kNoallocGElems = kNoallocMaxFft + (int64_t(1) << kMaxLog2);
 
-// Scratch: column-major copy of the input pairs, the FFT intermediate, and
-// the per-call constants.  4.06 MB + 4 MB + a few hundred bytes per device.
+// Scratch: column-major copy of the input pairs, the FFT intermediate, the
+// twiddle tables and the per-call constants: 4.06 MB + 4 MB + 16 KB per device.
 static __device__ __align__(256) float4 g_scratch_G[kNoallocGElems];
 static __device__ __align__(256) float4 g_scratch_Z[kNoallocMaxFft];
+static __device__ __align__(256) float2 g_scratch_tw[4 * (1 << (kNoallocMaxLog2 / 2))];
 static __device__ __align__(256) SkyConst g_scratch_sky;
 static __device__ __align__(256) TmplCoef g_scratch_coef;
 
@@ -37,6 +38,7 @@ constexpr int kMaxDevices = 64;
 struct DevPtrs {
   float4* G;
   float4* Z;
+  float2* tw;
   SkyConst* sky;
   TmplCoef* coef;
 };
@@ -56,6 +58,7 @@ int device_ptrs(DevPtrs* out) {
       DevPtrs p{};
       if (cudaGetSymbolAddress((void**)&p.G, g_scratch_G) != cudaSuccess) return FSTAT_ERR_CUDA;
       if (cudaGetSymbolAddress((void**)&p.Z, g_scratch_Z) != cudaSuccess) return FSTAT_ERR_CUDA;
+      if (cudaGetSymbolAddress((void**)&p.tw, g_scratch_tw) != cudaSuccess) return FSTAT_ERR_CUDA;
       if (cudaGetSymbolAddress((void**)&p.sky, g_scratch_sky) != cudaSuccess) return FSTAT_ERR_CUDA;
       if (cudaGetSymbolAddress((void**)&p.coef, g_scratch_coef) != cudaSuccess) return FSTAT_ERR_CUDA;
       g_ptrs[dev] = p;
@@ -143,9 +146,12 @@ extern "C" int fstat_twoF_noalloc(const void* g_pairs, int64_t n_samples, int64_
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_noalloc_columns<<<blocks, 256, 0, st>>>((const float4*)g_pairs, n_samples, n1, lc, p.G);
   if (cudaGetLastError() != cudaSuccess) return FSTAT_ERR_CUDA;
-  cudaError_t e = launch_pass_a_f32(log2n2, p.G, lc, n_samples, n1, log2n, p.coef, p.Z, st);
+  cudaError_t e = build_twiddles(FSTAT_MIXED, log2n1, log2n2, p.tw, st);
   if (e != cudaSuccess) return FSTAT_ERR_CUDA;
-  e = launch_pass_b_f32(log2n1, p.Z, n2, p.sky, twoF, st);
+  TwiddleTables tt = twiddle_layout(FSTAT_MIXED, log2n1, log2n2, p.tw);
+  e = launch_pass_a_f32(log2n2, 0, 0, p.G, lc, n_samples, n1, tt.a, tt.hi, tt.lo, tt.h, p.coef, p.Z, st);
+  if (e != cudaSuccess) return FSTAT_ERR_CUDA;
+  e = launch_pass_b_f32(log2n1, 0, 0, p.Z, n2, tt.b, p.sky, twoF, st);
   if (e != cudaSuccess) return FSTAT_ERR_CUDA;
   return FSTAT_OK;
 }

@@ -8,10 +8,15 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "fstat_internal.cuh"
@@ -38,6 +43,10 @@ struct fstat_plan {
   double* partials = nullptr;
   int nblk = 0;
   SkyConst* sky = nullptr;
+  void* tw = nullptr;            // twiddle tables for the current split
+  TwiddleTables tt{};
+  int ca = 0, cb = 0;            // CTA shapes of pass A / pass B (0 = default)
+  int va = 0, vb = 0;            // radix schedules of pass A / pass B
   int* d_err = nullptr;   // [0] sticky kernel error, [1] scratch for input checks
   int* h_err = nullptr;   // pinned
   fstat_template* d_tmpl = nullptr;
@@ -86,6 +95,7 @@ void free_all(fstat_plan* p) {
   if (p->Z) cudaFree(p->Z);
   if (p->partials) cudaFree(p->partials);
   if (p->sky) cudaFree(p->sky);
+  if (p->tw) cudaFree(p->tw);
   if (p->d_err) cudaFree(p->d_err);
   if (p->h_err) cudaFreeHost(p->h_err);
   if (p->d_tmpl) cudaFree(p->d_tmpl);
@@ -154,7 +164,26 @@ int set_split(fstat_plan* p, int log2n1) {
   p->n2 = int64_t(1) << log2n2;
   p->lc = (p->d.n_samples + p->n1 - 1) / p->n1;
   p->sky_valid = false;
+  if (p->tw) {
+    p->tt = twiddle_layout(p->d.precision, log2n1, log2n2, p->tw);
+    CK(build_twiddles(p->d.precision, log2n1, log2n2, p->tw, 0));
+    CK(cudaStreamSynchronize(0));
+  }
   return FSTAT_OK;
+}
+
+cudaError_t launch_a(fstat_plan* p, int ca, int va, const TmplCoef* coef, cudaStream_t st) {
+  const TwiddleTables& t = p->tt;
+  return p->d.precision == FSTAT_FP64
+      ? launch_pass_a_f64(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, p->Z, st)
+      : launch_pass_a_f32(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, p->Z, st);
+}
+
+cudaError_t launch_b(fstat_plan* p, int cb, int vb, float* out, cudaStream_t st) {
+  const TwiddleTables& t = p->tt;
+  return p->d.precision == FSTAT_FP64
+      ? launch_pass_b_f64(p->log2n1, cb, vb, p->Z, (int)p->n2, t.b, p->sky, out, st)
+      : launch_pass_b_f32(p->log2n1, cb, vb, p->Z, (int)p->n2, t.b, p->sky, out, st);
 }
 
 }  // namespace
@@ -233,6 +262,7 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   if (e == cudaSuccess) e = cudaMalloc(&p->Z, (size_t)d.n_fft * p->pair_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->partials, (size_t)3 * p->nblk * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->sky, sizeof(SkyConst));
+  if (e == cudaSuccess) e = cudaMalloc(&p->tw, (size_t)4 * (size_t(1) << kMaxLog2) * 16);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_err, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_err, 2 * sizeof(int));
@@ -242,6 +272,12 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
     free_all(p);
     delete p;
     return cuda_status(e);
+  }
+  int rc = set_split(p, p->log2n1);
+  if (rc) {
+    free_all(p);
+    delete p;
+    return rc;
   }
   *out = p;
   return FSTAT_OK;
@@ -328,17 +364,13 @@ int fstat_compute(fstat_plan* p, const fstat_template* tmpl, int64_t n_tmpl, flo
       const TmplCoef* coef = p->d_coef + k;
       EventPair ea{}, eb{};
       if (p->prof) { ea = get_events(p); cudaEventRecord(ea.a, st); }
-      cudaError_t e = p->d.precision == FSTAT_FP64
-          ? launch_pass_a_f64(p->log2n2, p->G, p->lc, p->d.n_samples, (int)p->n1, p->log2n, coef, p->Z, st)
-          : launch_pass_a_f32(p->log2n2, p->G, p->lc, p->d.n_samples, (int)p->n1, p->log2n, coef, p->Z, st);
+      cudaError_t e = launch_a(p, p->ca, p->va, coef, st);
       if (e != cudaSuccess) return cuda_status(e);
       if (p->prof) {
         cudaEventRecord(ea.b, st); p->ev[0].push_back(ea); p->launches[0]++;
         eb = get_events(p); cudaEventRecord(eb.a, st);
       }
-      e = p->d.precision == FSTAT_FP64
-          ? launch_pass_b_f64(p->log2n1, p->Z, (int)p->n2, p->sky, out, st)
-          : launch_pass_b_f32(p->log2n1, p->Z, (int)p->n2, p->sky, out, st);
+      e = launch_b(p, p->cb, p->vb, out, st);
       if (e != cudaSuccess) return cuda_status(e);
       if (p->prof) { cudaEventRecord(eb.b, st); p->ev[1].push_back(eb); p->launches[1]++; }
     }
@@ -443,4 +475,159 @@ int fstat_set_split(fstat_plan* p, int64_t n1) {
   return set_split(p, l);
 }
 
+int fstat_get_cta(const fstat_plan* p, int* ca, int* va, int* cb, int* vb) {
+  if (!p || !ca || !va || !cb || !vb) return FSTAT_ERR_INVALID_ARG;
+  *ca = p->ca;
+  *va = p->va;
+  *cb = p->cb;
+  *vb = p->vb;
+  return FSTAT_OK;
+}
+
+int fstat_set_cta(fstat_plan* p, int ca, int va, int cb, int vb) {
+  if (!p || ca < 0 || cb < 0 || ca > 32 || cb > 32 || va < 0 || va > 1 || vb < 0 || vb > 1)
+    return FSTAT_ERR_INVALID_ARG;
+  p->ca = ca;
+  p->va = va;
+  p->cb = cb;
+  p->vb = vb;
+  return FSTAT_OK;
+}
+
 }  // extern "C"
+
+// ------------------------------------------------------------------ autotune
+namespace {
+
+struct Choice {
+  int l1, ca, va, cb, vb;
+};
+std::mutex g_tune_mu;
+std::map<std::string, Choice> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+std::string tune_key(const fstat_plan* p) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) prop.name[0] = 0;
+  char buf[400];
+  std::snprintf(buf, sizeof buf, "%s|N=%lld|nfft=%lld|prec=%d|ndet=%d", prop.name,
+                (long long)p->d.n_samples, (long long)p->d.n_fft, p->d.precision, p->d.n_det);
+  for (char* c = buf; *c; ++c)
+    if (*c == ' ' || *c == '\t') *c = '_';
+  return buf;
+}
+
+void load_tune_file() {
+  if (g_tune_file_loaded) return;
+  g_tune_file_loaded = true;
+  const char* f = std::getenv("FSTAT_AUTOTUNE_CACHE");
+  if (!f) return;
+  std::ifstream in(f);
+  std::string key;
+  Choice c;
+  while (in >> key >> c.l1 >> c.ca >> c.va >> c.cb >> c.vb) g_tune_cache[key] = c;
+}
+
+void save_tune(const std::string& key, const Choice& c) {
+  g_tune_cache[key] = c;
+  const char* f = std::getenv("FSTAT_AUTOTUNE_CACHE");
+  if (!f) return;
+  std::ofstream out(f, std::ios::app);
+  out << key << " " << c.l1 << " " << c.ca << " " << c.va << " " << c.cb << " " << c.vb << "\n";
+}
+
+// mean time (ms) of `reps` launches of pass A (which = 0) or pass B (which = 1)
+float time_pass(fstat_plan* p, int which, int c, int v, const TmplCoef* coef, float* out, cudaStream_t st,
+                cudaEvent_t e0, cudaEvent_t e1) {
+  const int reps = 5;
+  cudaError_t e = which == 0 ? launch_a(p, c, v, coef, st) : launch_b(p, c, v, out, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return -1.f;
+  }
+  cudaEventRecord(e0, st);
+  for (int r = 0; r < reps; ++r) {
+    if (which == 0) launch_a(p, c, v, coef, st);
+    else launch_b(p, c, v, out, st);
+  }
+  cudaEventRecord(e1, st);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms / reps;
+}
+
+}  // namespace
+
+extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
+  if (!p) return FSTAT_ERR_INVALID_ARG;
+  for (int X = 0; X < p->d.n_det; ++X)
+    if (!p->have[X]) return FSTAT_ERR_NOT_READY;
+  cudaStream_t st = (cudaStream_t)stream;
+  const std::string key = tune_key(p);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    load_tune_file();
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      CK(cudaDeviceSynchronize());
+      int rc = set_split(p, it->second.l1);
+      if (rc) return rc;
+      p->ca = it->second.ca;
+      p->va = it->second.va;
+      p->cb = it->second.cb;
+      p->vb = it->second.vb;
+      return FSTAT_OK;
+    }
+  }
+  int rc = ensure_capacity(p, 1);
+  if (rc) return rc;
+  if (p->staged_pending) { CK(cudaEventSynchronize(p->staged)); p->staged_pending = false; }
+  p->h_tmpl[0] = fstat_template{0.3, -0.5, -1e-10, 0.0};
+  p->h_order[0] = 0;
+  CK(cudaMemcpyAsync(p->d_tmpl, p->h_tmpl, sizeof(fstat_template), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(p->d_order, p->h_order, sizeof(int), cudaMemcpyHostToDevice, st));
+  float* out = nullptr;
+  CK(cudaMalloc(&out, (size_t)p->d.n_fft * sizeof(float)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int lo = std::max(kMinLog2, p->log2n - kMaxLog2), hi = std::min(kMaxLog2, p->log2n - kMinLog2);
+  Choice best{p->log2n1, 0, 0, 0, 0};
+  float best_ms = 1e30f;
+  static const int kCa[] = {0, 1, 2, 4};
+  static const int kCb[] = {0, 1, 2, 4, 8};
+  for (int l1 = lo; l1 <= hi && rc == FSTAT_OK; ++l1) {
+    rc = set_split(p, l1);
+    if (rc) break;
+    rc = run_sky(p, 0.3, -0.5, st);
+    if (rc) break;
+    launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, 0, 1, p->d_coef, st);
+    float ba = 1e30f, bb = 1e30f;
+    int ca = 0, cb = 0, va = 0, vb = 0;
+    for (int v = 0; v < 2; ++v) {
+      for (int c : kCa) {
+        float ms = time_pass(p, 0, c, v, p->d_coef, out, st, e0, e1);
+        if (ms > 0.f && ms < ba) { ba = ms; ca = c; va = v; }
+      }
+      for (int c : kCb) {
+        float ms = time_pass(p, 1, c, v, p->d_coef, out, st, e0, e1);
+        if (ms > 0.f && ms < bb) { bb = ms; cb = c; vb = v; }
+      }
+    }
+    if (ba + bb < best_ms) { best_ms = ba + bb; best = Choice{l1, ca, va, cb, vb}; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (rc) return rc;
+  rc = set_split(p, best.l1);
+  if (rc) return rc;
+  p->ca = best.ca;
+  p->va = best.va;
+  p->cb = best.cb;
+  p->vb = best.vb;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  save_tune(key, best);
+  return FSTAT_OK;
+}
