@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-refine", action="store_true")
     return ap.parse_args()
 
 
@@ -317,6 +318,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_fp64:
         line["fp64_gpu"] = fp64_gpu(t, xs, tm_all, args.fp64_templates, dev, stream, value)
 
+    # differentiable refinement: 4096 candidates x 20 gradient-ascent steps
+    if rank == 0 and not args.no_refine:
+        line["refine"] = refine_bench(t, xs, dev)
+
     # end-to-end: host x_h (pinned) -> device, compute, 2F back to pinned host
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(t, xs, tm, chunk, dev, stream, args)
@@ -356,6 +361,38 @@ def fp64_gpu(t, xs, tm_all, n, dev, stream, mixed_value):
     v = total / ((ms_sky + total * per_t) / 1e3)
     return {"value": v, "unit": UNIT, "sample": f"per-sky step + {n} templates, extrapolated to {total}",
             "mixed_over_fp64": mixed_value / v}
+
+
+def refine_bench(t, xs, dev, n_cand=4096, steps=20):
+    """Adjoint throughput: 2F + gradient evaluations of off-grid candidates
+    (half a grid step around bank points) during 20 ascent steps."""
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+    from paper_2201_00451_gb300 import refine as rf
+
+    plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
+    for X in range(len(t.detectors)):
+        plan.set_data(X, xs[X], t.sigmas[X])
+    rng = np.random.Generator(np.random.PCG64(t.seed))
+    tm = t.templates()
+    pick = rng.integers(0, len(tm), n_cand)
+    half = t.n_fft // 2
+    f = t.freq(rng.integers(half - int(0.4 * t.n_fft), half + int(0.4 * t.n_fft), n_cand))
+    scales = np.array([1.0 / t.t_span, 1.0 / t.t_span ** 2, np.radians(1.0 / 60.0), np.radians(1.0 / 60.0)])
+    theta0 = np.stack([f, tm["f1dot"][pick], tm["alpha"][pick], tm["delta"][pick]], axis=1)
+    theta0 = theta0 + rng.uniform(-0.5, 0.5, theta0.shape) * scales
+    rf.refine(plan, theta0[:64], scales, steps=2)          # warm-up (builds sample tables)
+    torch.cuda.synchronize(dev)
+    s = time.perf_counter()
+    _, hist = rf.refine(plan, theta0, scales, steps=steps)
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - s
+    plan.close()
+    evals = n_cand * (steps + 1)
+    return {"value": evals / el, "unit": "2F+gradient evaluations/s", "candidates": n_cand,
+            "steps": steps, "seconds": el, "samples_per_eval": t.n_samples * len(t.detectors),
+            "mean_2F_gain": float((hist[-1] - hist[0]).mean())}
 
 
 def e2e(t, xs, tm, chunk, dev, stream, args):

@@ -94,6 +94,11 @@ typedef struct {
   double alpha, delta, f1dot, f2dot;
 } fstat_template;
 
+/* A refinement candidate: frequency at t_ref, spindowns, sky position. */
+typedef struct {
+  double f, f1dot, alpha, delta, f2dot;
+} fstat_candidate;
+
 typedef struct fstat_plan fstat_plan;
 
 /* Create a plan on the current CUDA device.  Allocates all device buffers
@@ -122,6 +127,20 @@ int fstat_set_data(fstat_plan* plan, int det, const void* xh, int dtype, int64_t
  * DEGENERATE is reported by fstat_sync. */
 int fstat_compute(fstat_plan* plan, const fstat_template* tmpl, int64_t n_tmpl, float* twoF,
                   void* stream);
+
+/* 2F and its gradient at arbitrary (off-grid) parameters, for refinement.
+ * For each candidate, eq. (Fstat) is evaluated with the demodulation
+ * integrals of eqs. (Fa_DET)/(Fb_DET) (Sec. 2) summed directly over the
+ * detector samples at the single frequency f (no resampling, no FFT):
+ *   Phi_k = (f - f_h) tau_k + f_h t_m(t_k) + f1dot tau_k^2/2 + f2dot tau_k^3/6,
+ *   tau_k = t_k + t_m(t_k) - t_ref,  Fa = sum_X w_X sum_k x a e^{-i 2 pi Phi_k}.
+ * `cand` is a HOST array of n candidates; `twoF` (n floats) and `grad`
+ * (n x 4 floats: d2F/df, d2F/df1dot, d2F/dalpha, d2F/ddelta) are caller-
+ * owned DEVICE buffers.  f2dot is held fixed.  The first call after data
+ * changes builds sample tables (24 + 32 B per sample and detector).
+ * Errors: INVALID_ARG, NOT_READY, OOM, CUDA. */
+int fstat_grad(fstat_plan* plan, const fstat_candidate* cand, int64_t n, float* twoF, float* grad,
+               void* stream);
 
 /* Frequency axis of the output: f_m = *f0 + m * *df. */
 int fstat_freq_axis(const fstat_plan* plan, double* f0, double* df);

@@ -14,10 +14,12 @@ continuous gravitational wave searches", arXiv:2201.00451):
                    directly over detector samples (the exact definition).
 * ``synth``     -- CW signal injection into seeded noise.
 * ``metrics``   -- the comparison metrics r1, r2, theta of Sec. 4.2.
+* ``grad``      -- 2F and its gradient in (f, f1dot, alpha, delta) at
+                   arbitrary parameters, from the demodulation sums.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA
 library and never imports it.
 """
 
-from . import geometry, resamp, demod, synth, metrics  # noqa: F401
+from . import geometry, resamp, demod, synth, metrics, grad  # noqa: F401

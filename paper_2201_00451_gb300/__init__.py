@@ -42,6 +42,7 @@ EXPORTS = (
     "fstat_invalidate_sky", "fstat_export_sky", "fstat_sync", "fstat_set_profiling",
     "fstat_kernel_stats", "fstat_get_split", "fstat_set_split", "fstat_plan_destroy",
     "fstat_strerror", "fstat_twoF_noalloc", "fstat_get_cta", "fstat_set_cta", "fstat_autotune",
+    "fstat_grad",
 )
 
 
@@ -80,6 +81,8 @@ class Template(ctypes.Structure):
 
 
 TEMPLATE_DTYPE = np.dtype([("alpha", "<f8"), ("delta", "<f8"), ("f1dot", "<f8"), ("f2dot", "<f8")])
+CANDIDATE_DTYPE = np.dtype([("f", "<f8"), ("f1dot", "<f8"), ("alpha", "<f8"), ("delta", "<f8"),
+                            ("f2dot", "<f8")])
 
 _lib = None
 
@@ -113,6 +116,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fstat_get_cta": (i32, [P] + [ctypes.POINTER(i32)] * 4),
         "fstat_set_cta": (i32, [P, i32, i32, i32, i32]),
         "fstat_autotune": (i32, [P, P]),
+        "fstat_grad": (i32, [P, P, i64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -253,6 +257,19 @@ class FstatPlan:
         rc = self._lib.fstat_compute(self._p, ctypes.c_void_p(templates.ctypes.data), len(templates),
                                      ctypes.c_void_p(out_ptr), _stream_handle(stream))
         _check(rc, "fstat_compute")
+
+    def grad(self, candidates, stream=None):
+        """fstat_grad: (2F [n], d2F/d(f, f1dot, alpha, delta) [n, 4]) as CUDA
+        float32 tensors for a structured array of CANDIDATE_DTYPE."""
+        import torch
+        c = np.ascontiguousarray(candidates, dtype=CANDIDATE_DTYPE)
+        n = len(c)
+        two_f = torch.empty(n, dtype=torch.float32, device="cuda")
+        g = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        rc = self._lib.fstat_grad(self._p, ctypes.c_void_p(c.ctypes.data), n, ctypes.c_void_p(two_f.data_ptr()),
+                                  ctypes.c_void_p(g.data_ptr()), _stream_handle(stream))
+        _check(rc, "fstat_grad")
+        return two_f, g
 
     def freq_axis(self):
         f0, df = ctypes.c_double(), ctypes.c_double()

@@ -34,6 +34,18 @@ namespace fft {
 // -DFSTAT_PASSB_TABLE=1) measured 11% slower on GB300 at n_fft = 2^22.
 constexpr bool kPassBTable = FSTAT_PASSB_TABLE != 0;
 
+#ifndef FSTAT_PIPELINE
+#define FSTAT_PIPELINE 1
+#endif
+#ifndef FSTAT_R8_MINB
+#define FSTAT_R8_MINB 1
+#endif
+// FSTAT_PIPELINE = 1: persistent CTAs prefetch the next tile with cp.async;
+// 0: one tile per CTA, loaded straight into registers.
+constexpr bool kPipeline = FSTAT_PIPELINE != 0;
+// minimum resident CTAs requested for radix-8 variants (0 = no register cap)
+constexpr int kR8MinBlocks = FSTAT_R8_MINB;
+
 template <typename T> struct TwT;
 template <> struct TwT<float> { using type = float2; };
 template <> struct TwT<double> { using type = double2; };
@@ -75,10 +87,34 @@ template <typename T, int L, int V = 0> struct Shape {
   using TW = typename TwT<T>::type;
 };
 
+// Shared memory of a persistent pass kernel: NBUF padded buffers of C
+// columns; two (prefetch the next tile while transforming this one) when
+// they fit, else one.
+constexpr size_t kSmemCap = (size_t)220 * 1024;
+template <typename T, int L, int C, int V = 0> struct Buf {
+  static constexpr size_t ONE = (size_t)C * Shape<T, L, V>::LP * sizeof(typename Shape<T, L, V>::PM);
+  static constexpr int NBUF = (kPipeline && 2 * ONE <= kSmemCap) ? 2 : 1;
+  static constexpr size_t BYTES = NBUF * ONE;
+};
+
 template <typename T, int L, int C, int V = 0> constexpr bool cfg_ok() {
   using S = Shape<T, L, V>;
-  return C * S::TPC >= 32 && C * S::TPC <= 1024 &&
-         (size_t)C * S::LP * sizeof(typename S::PM) <= (size_t)200 * 1024;
+  return C * S::TPC >= 32 && C * S::TPC <= 1024 && Buf<T, L, C, V>::ONE <= kSmemCap;
+}
+
+// 16-byte asynchronous global -> shared copies (completion tracked by
+// commit groups; cp.async.wait_group is a hardware wait, not a spin loop).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+template <typename PM> __device__ __forceinline__ void cp_pair(PM* dst, const PM* src) {
+  cp_async16(dst, src);
+  if constexpr (sizeof(PM) == 32) cp_async16((char*)dst + 16, (const char*)src + 16);
 }
 
 __device__ __forceinline__ int pad_idx(int pos, int ps) { return pos + (pos >> ps); }
@@ -267,30 +303,26 @@ __device__ __forceinline__ void spin_rot(const TmplCoef& c, int si, double* cs, 
 }
 
 // ------------------------------------------------------------- pass A
-template <typename T, int L, int CA, int V>
-__global__ void __launch_bounds__(CA * Shape<T, L, V>::TPC)
-k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int n1,
-         const typename TwT<T>::type* __restrict__ twL, const typename TwT<T>::type* __restrict__ tw_hi,
-         const typename TwT<T>::type* __restrict__ tw_lo, int h, const TmplCoef* __restrict__ coefp,
-         typename PairMem<T>::type* __restrict__ Z) {
+// One tile = CA columns.  `staged`: the column samples were copied to `buf`
+// (at padded natural positions) by cp.async; otherwise they are loaded from
+// global memory straight into registers.
+template <typename T, int L, int CA, int V, bool STAGED>
+__device__ __forceinline__ void pass_a_tile(int tile, typename PairMem<T>::type* buf, int c, int t,
+                                            const typename PairMem<T>::type* __restrict__ G, int64_t lc,
+                                            int n, int n1, const typename TwT<T>::type* __restrict__ twL,
+                                            const TmplCoef& tc, T inv_n,
+                                            typename PairMem<T>::type* __restrict__ Z) {
   using S = Shape<T, L, V>;
   using PM = typename PairMem<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  PM* smem = reinterpret_cast<PM*>(smem_raw);
-  const int c = threadIdx.x / S::TPC;
-  const int t = threadIdx.x % S::TPC;
-  const int col = blockIdx.x * CA + c;
-  PM* buf = smem + c * S::LP;
-  const TmplCoef tc = *coefp;
+  const int col = tile * CA + c;
   const PM* gcol = G + (int64_t)col * lc;
-
   Pair<T> v[S::R0];
 #pragma unroll
   for (int s = 0; s < S::R0; ++s) {
     const int n2 = t + s * S::TPC;
     const int j = col + n1 * n2;
     if (j < n) {
-      Pair<T> g = pload_g(gcol + n2);
+      Pair<T> g = STAGED ? pload(buf + pad_idx(n2, S::PS)) : pload_g(gcol + n2);
       T cs, sn;
       spin_rot(tc, j - tc.J, &cs, &sn);
       v[s] = pmul(g, cs, sn);
@@ -298,14 +330,13 @@ k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int
       v[s] = pzero<T>();
     }
   }
+  if constexpr (STAGED) __syncthreads();  // the staged column is overwritten below
   dft<T, S::R0>(v);
   store_pass0<T, L, V, 1>(v, buf, t);
   passes<T, L, V, 1, 1, false>(v, buf, t, twL);
 
   // four-step twiddle W_N^{col k2} = W_N^{col b} (W_N^{col NSL})^s for
   // k2 = b + s * NSL, and store Z[col][k2]
-  const int log2N = log2c(L) + 31 - __clz(n1);
-  const T inv_n = (T)1 / (T)(1 << log2N);
   T sc, ss, stc[S::RL], sts[S::RL];
   turn_sincos(-(T)(col * S::NSL) * inv_n, &ss, &sc);
   powers<T, S::RL>(sc, ss, stc, sts);
@@ -324,34 +355,89 @@ k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int
       pstore(zrow + b + s * S::NSL, pmul(x[s], wc, ws));
     }
   }
-  (void)tw_hi; (void)tw_lo; (void)h;
 }
 
-// ------------------------------------------------------------- pass B
-template <typename T, int L, int CB, int V>
-__global__ void __launch_bounds__(CB * Shape<T, L, V>::TPC)
-k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
-         const typename TwT<T>::type* __restrict__ twL, const SkyConst* __restrict__ sky,
-         float* __restrict__ out) {
+template <typename T, int L, int C, int V> constexpr int min_blocks() {
+  // radix-8 variants: ask for enough resident CTAs to cap registers at 64
+  constexpr int threads = C * Shape<T, L, V>::TPC;
+  constexpr int want = 65536 / (threads * 64);
+  return (V == 1 && kR8MinBlocks > 0 && want > 1) ? want : 1;
+}
+
+// Direct mode (kPipeline = false): one tile per CTA.  Pipelined mode: the
+// CTA transforms tiles b, b + grid, ...; the next tile's samples are copied
+// asynchronously into the other buffer while the current one is
+// transformed in place.
+template <typename T, int L, int CA, int V>
+__global__ void __launch_bounds__(CA * Shape<T, L, V>::TPC, (min_blocks<T, L, CA, V>()))
+k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int n1,
+         const typename TwT<T>::type* __restrict__ twL, const TmplCoef* __restrict__ coefp,
+         typename PairMem<T>::type* __restrict__ Z) {
   using S = Shape<T, L, V>;
+  using B = Buf<T, L, CA, V>;
   using PM = typename PairMem<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PM* smem = reinterpret_cast<PM*>(smem_raw);
-  const int c = threadIdx.x % CB;
-  const int t = threadIdx.x / CB;
-  const int k2 = blockIdx.x * CB + c;
-  PM* buf = smem + c;
+  const int c = threadIdx.x / S::TPC;
+  const int t = threadIdx.x % S::TPC;
+  const TmplCoef tc = *coefp;
+  const int log2N = log2c(L) + 31 - __clz(n1);
+  const T inv_n = (T)1 / (T)(1 << log2N);
+  if constexpr (!kPipeline) {
+    pass_a_tile<T, L, CA, V, false>(blockIdx.x, smem + c * S::LP, c, t, G, lc, n, n1, twL, tc, inv_n, Z);
+  } else {
+    const int n_tiles = n1 / CA;
+    auto stage = [&](int it) { return smem + (B::NBUF == 2 ? (it & 1) : 0) * (CA * S::LP) + c * S::LP; };
+    auto prefetch = [&](int tile, PM* dst) {
+      const int col = tile * CA + c;
+      const PM* gcol = G + (int64_t)col * lc;
+#pragma unroll
+      for (int s = 0; s < S::R0; ++s) {
+        const int n2 = t + s * S::TPC;
+        if (col + n1 * n2 < n) cp_pair(dst + pad_idx(n2, S::PS), gcol + n2);
+      }
+    };
+    int tile = blockIdx.x;
+    if constexpr (B::NBUF == 2) {
+      if (tile < n_tiles) prefetch(tile, stage(0));
+      cp_async_commit();
+    }
+    for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
+      PM* buf = stage(it);
+      if constexpr (B::NBUF == 2) {
+        if (tile + (int)gridDim.x < n_tiles) prefetch(tile + gridDim.x, stage(it + 1));
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        prefetch(tile, buf);
+        cp_async_commit();
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      pass_a_tile<T, L, CA, V, true>(tile, buf, c, t, G, lc, n, n1, twL, tc, inv_n, Z);
+      __syncthreads();  // this buffer is the prefetch target two tiles on
+    }
+  }
+}
 
+// ------------------------------------------------------------- pass B
+template <typename T, int L, int CB, int V, bool STAGED>
+__device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type* buf, int c, int t,
+                                            const typename PairMem<T>::type* __restrict__ Z, int n2,
+                                            const typename TwT<T>::type* __restrict__ twL, T kA, T kB, T kC,
+                                            float* __restrict__ out) {
+  using S = Shape<T, L, V>;
+  const int k2 = tile * CB + c;
   Pair<T> v[S::R0];
 #pragma unroll
-  for (int s = 0; s < S::R0; ++s) v[s] = pload_g(Z + (int64_t)(t + s * S::TPC) * n2 + k2);
+  for (int s = 0; s < S::R0; ++s)
+    v[s] = STAGED ? pload(buf + pad_idx(t + s * S::TPC, S::PS) * CB)
+                  : pload_g(Z + (int64_t)(t + s * S::TPC) * n2 + k2);
+  if constexpr (STAGED) __syncthreads();  // the staged rows are overwritten below
   dft<T, S::R0>(v);
   store_pass0<T, L, V, CB>(v, buf, t);
   passes<T, L, V, CB, 1, kPassBTable && sizeof(T) == 4>(v, buf, t, twL);
 
-  T kA, kB, kC;
-  if constexpr (sizeof(T) == 4) { kA = sky->kAf; kB = sky->kBf; kC = sky->kCf; }
-  else { kA = sky->kA; kB = sky->kB; kC = sky->kC; }
   constexpr int NB = S::R0 / S::RL;
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
@@ -370,38 +456,108 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
   }
 }
 
+template <typename T, int L, int CB, int V>
+__global__ void __launch_bounds__(CB * Shape<T, L, V>::TPC, (min_blocks<T, L, CB, V>()))
+k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
+         const typename TwT<T>::type* __restrict__ twL, const SkyConst* __restrict__ sky,
+         float* __restrict__ out) {
+  using S = Shape<T, L, V>;
+  using B = Buf<T, L, CB, V>;
+  using PM = typename PairMem<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PM* smem = reinterpret_cast<PM*>(smem_raw);
+  const int c = threadIdx.x % CB;
+  const int t = threadIdx.x / CB;
+  T kA, kB, kC;
+  if constexpr (sizeof(T) == 4) { kA = sky->kAf; kB = sky->kBf; kC = sky->kCf; }
+  else { kA = sky->kA; kB = sky->kB; kC = sky->kC; }
+  if constexpr (!kPipeline) {
+    pass_b_tile<T, L, CB, V, false>(blockIdx.x, smem + c, c, t, Z, n2, twL, kA, kB, kC, out);
+  } else {
+    const int n_tiles = n2 / CB;
+    auto stage = [&](int it) { return smem + (B::NBUF == 2 ? (it & 1) : 0) * (CB * S::LP) + c; };
+    auto prefetch = [&](int tile, PM* dst) {
+      const int k2 = tile * CB + c;
+#pragma unroll
+      for (int s = 0; s < S::R0; ++s) {
+        const int n1 = t + s * S::TPC;
+        cp_pair(dst + pad_idx(n1, S::PS) * CB, Z + (int64_t)n1 * n2 + k2);
+      }
+    };
+    int tile = blockIdx.x;
+    if constexpr (B::NBUF == 2) {
+      if (tile < n_tiles) prefetch(tile, stage(0));
+      cp_async_commit();
+    }
+    for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
+      PM* buf = stage(it);
+      if constexpr (B::NBUF == 2) {
+        if (tile + (int)gridDim.x < n_tiles) prefetch(tile + gridDim.x, stage(it + 1));
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        prefetch(tile, buf);
+        cp_async_commit();
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      pass_b_tile<T, L, CB, V, true>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out);
+      __syncthreads();  // this buffer is the prefetch target two tiles on
+    }
+  }
+}
+
 // ------------------------------------------------------------- launchers
+// Resident CTAs of a persistent kernel: SM count x CTAs per SM (queried
+// once per kernel instantiation).
+template <typename K>
+cudaError_t resident_ctas(K kernel, int threads, size_t smem, int* out) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  *out = sms * per_sm;
+  return cudaSuccess;
+}
+
 template <typename T, int L, int CA, int V>
 cudaError_t run_a(const void* G, int64_t lc, int64_t n, int n1, const void* twA, const void* hi,
                   const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st) {
   using S = Shape<T, L, V>;
-  constexpr size_t smem = (size_t)CA * S::LP * sizeof(typename S::PM);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_pass_a<T, L, CA, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr size_t smem = Buf<T, L, CA, V>::BYTES;
+  constexpr int threads = CA * S::TPC;
+  static int ctas = 0;
+  if (!ctas) {
+    cudaError_t e = resident_ctas(k_pass_a<T, L, CA, V>, threads, smem, &ctas);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   if (n1 % CA) return cudaErrorInvalidConfiguration;
+  const int tiles = n1 / CA;
   using TW = typename S::TW;
-  k_pass_a<T, L, CA, V><<<n1 / CA, CA * S::TPC, smem, st>>>(
-      (const typename S::PM*)G, lc, (int)n, n1, (const TW*)twA, (const TW*)hi, (const TW*)lo, h, coef,
-      (typename S::PM*)Z);
+  const int grid = (!kPipeline || tiles < ctas) ? tiles : ctas;
+  k_pass_a<T, L, CA, V><<<grid, threads, smem, st>>>(
+      (const typename S::PM*)G, lc, (int)n, n1, (const TW*)twA, coef, (typename S::PM*)Z);
+  (void)hi; (void)lo; (void)h;
   return cudaGetLastError();
 }
 
 template <typename T, int L, int CB, int V>
 cudaError_t run_b(const void* Z, int n2, const void* twB, const SkyConst* sky, float* out, cudaStream_t st) {
   using S = Shape<T, L, V>;
-  constexpr size_t smem = (size_t)CB * S::LP * sizeof(typename S::PM);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_pass_b<T, L, CB, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr size_t smem = Buf<T, L, CB, V>::BYTES;
+  constexpr int threads = CB * S::TPC;
+  static int ctas = 0;
+  if (!ctas) {
+    cudaError_t e = resident_ctas(k_pass_b<T, L, CB, V>, threads, smem, &ctas);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   if (n2 % CB) return cudaErrorInvalidConfiguration;
-  k_pass_b<T, L, CB, V><<<n2 / CB, CB * S::TPC, smem, st>>>(
+  const int tiles = n2 / CB;
+  const int grid = (!kPipeline || tiles < ctas) ? tiles : ctas;
+  k_pass_b<T, L, CB, V><<<grid, threads, smem, st>>>(
       (const typename S::PM*)Z, n2, (const typename S::TW*)twB, sky, out);
   return cudaGetLastError();
 }

@@ -44,7 +44,8 @@ struct Geo {
   double c, au, r_earth, w_rot, w_orb, cos_obl, sin_obl, orb_ph0, sid_ph0;
   double lat[kMaxDet], lon[kMaxDet], gam[kMaxDet];
   double rcl[kMaxDet], rsl[kMaxDet];   // r_earth cos(lat), r_earth sin(lat)
-  double w[kMaxDet];                   // noise weights 1/(2 sigma^2)
+  double w[kMaxDet];                   // noise weights of the rescaled series, sigma_ref^2 / (2 sigma_X^2)
+  double inv_sigma_ref;                // z is stored divided by sigma_ref (smallest sigma_X)
   double t0, dt, f_het, t_ref;
   int64_t n;                           // samples per detector
   int n_det, dterms;
@@ -105,6 +106,14 @@ void launch_sky(const Geo& g, int precision, double alpha, double delta, const v
 void launch_tmpl_coef(const SkyConst* sky, double dt, const fstat_template* tmpl,
                       const int* order, int first, int count, TmplCoef* out, cudaStream_t st);
 void launch_check_finite(const void* x, int dtype, int64_t n, int* err, cudaStream_t st);
+// Gradient (adjoint.cu): per-plan sample tables and per-call scratch.
+size_t grad_table_bytes(int n_det, int64_t n);
+cudaError_t launch_grad_tables(const Geo& g, const void* const* xh, const int* dtype, void* base,
+                               cudaStream_t st);
+size_t grad_scratch_bytes(int n_cand, const Geo& g);
+cudaError_t launch_grad(const Geo& g, const void* tables, const fstat_candidate* cand_dev, int n_cand,
+                        void* scratch, float* twoF, float* grad, cudaStream_t st);
+
 // Twiddle tables (tables.cu): pointers into one device block.
 struct TwiddleTables {
   const void* a;   // pass A Stockham roots, N2 entries

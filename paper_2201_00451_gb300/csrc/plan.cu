@@ -37,9 +37,14 @@ struct fstat_plan {
   void* xh[kMaxDet] = {};
   int dtype[kMaxDet] = {};
   bool have[kMaxDet] = {};
+  double sigma[kMaxDet] = {};
+  double sigma_ref = 1.0;        // common rescaling of the series (see sky.cu)
   void* z = nullptr;
   void* G = nullptr;
   void* Z = nullptr;
+  void* Z2 = nullptr;              // second intermediate: template pairs overlap on two streams
+  cudaStream_t side = nullptr;     // plan-owned stream for every other template
+  cudaEvent_t fork = nullptr, join = nullptr;
   double* partials = nullptr;
   int nblk = 0;
   SkyConst* sky = nullptr;
@@ -60,6 +65,16 @@ struct fstat_plan {
   bool staged_pending = false;
   bool sky_valid = false;
   double sky_alpha = 0, sky_delta = 0;
+  // refinement: sample tables (built lazily), candidate staging, scratch
+  void* gtab = nullptr;
+  bool gtab_valid = false;
+  fstat_candidate* h_cand = nullptr;  // pinned
+  fstat_candidate* d_cand = nullptr;
+  int64_t ccap = 0;
+  void* gscratch = nullptr;
+  size_t gscratch_bytes = 0;
+  cudaEvent_t cand_staged = nullptr;
+  bool cand_pending = false;
   // profiling (kernel kinds 0 = pass A, 1 = pass B, 2 = per-sky work)
   bool prof = false;
   std::vector<EventPair> ev[3];
@@ -93,6 +108,10 @@ void free_all(fstat_plan* p) {
   if (p->z) cudaFree(p->z);
   if (p->G) cudaFree(p->G);
   if (p->Z) cudaFree(p->Z);
+  if (p->Z2) cudaFree(p->Z2);
+  if (p->side) cudaStreamDestroy(p->side);
+  if (p->fork) cudaEventDestroy(p->fork);
+  if (p->join) cudaEventDestroy(p->join);
   if (p->partials) cudaFree(p->partials);
   if (p->sky) cudaFree(p->sky);
   if (p->tw) cudaFree(p->tw);
@@ -103,6 +122,11 @@ void free_all(fstat_plan* p) {
   if (p->d_coef) cudaFree(p->d_coef);
   if (p->h_tmpl) cudaFreeHost(p->h_tmpl);
   if (p->h_order) cudaFreeHost(p->h_order);
+  if (p->gtab) cudaFree(p->gtab);
+  if (p->h_cand) cudaFreeHost(p->h_cand);
+  if (p->d_cand) cudaFree(p->d_cand);
+  if (p->gscratch) cudaFree(p->gscratch);
+  if (p->cand_staged) cudaEventDestroy(p->cand_staged);
   if (p->staged) cudaEventDestroy(p->staged);
   if (p->done) cudaEventDestroy(p->done);
   for (auto& v : p->ev)
@@ -172,18 +196,20 @@ int set_split(fstat_plan* p, int log2n1) {
   return FSTAT_OK;
 }
 
-cudaError_t launch_a(fstat_plan* p, int ca, int va, const TmplCoef* coef, cudaStream_t st) {
+cudaError_t launch_a(fstat_plan* p, int ca, int va, const TmplCoef* coef, cudaStream_t st, void* Z = nullptr) {
   const TwiddleTables& t = p->tt;
+  if (!Z) Z = p->Z;
   return p->d.precision == FSTAT_FP64
-      ? launch_pass_a_f64(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, p->Z, st)
-      : launch_pass_a_f32(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, p->Z, st);
+      ? launch_pass_a_f64(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, Z, st)
+      : launch_pass_a_f32(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, Z, st);
 }
 
-cudaError_t launch_b(fstat_plan* p, int cb, int vb, float* out, cudaStream_t st) {
+cudaError_t launch_b(fstat_plan* p, int cb, int vb, float* out, cudaStream_t st, void* Z = nullptr) {
   const TwiddleTables& t = p->tt;
+  if (!Z) Z = p->Z;
   return p->d.precision == FSTAT_FP64
-      ? launch_pass_b_f64(p->log2n1, cb, vb, p->Z, (int)p->n2, t.b, p->sky, out, st)
-      : launch_pass_b_f32(p->log2n1, cb, vb, p->Z, (int)p->n2, t.b, p->sky, out, st);
+      ? launch_pass_b_f64(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st)
+      : launch_pass_b_f32(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st);
 }
 
 }  // namespace
@@ -260,6 +286,10 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   if (e == cudaSuccess) e = cudaMalloc(&p->z, (size_t)d.n_det * N * zb);
   if (e == cudaSuccess) e = cudaMalloc(&p->G, (size_t)(N + (int64_t(1) << kMaxLog2)) * p->pair_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->Z, (size_t)d.n_fft * p->pair_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->Z2, (size_t)d.n_fft * p->pair_bytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&p->partials, (size_t)3 * p->nblk * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->sky, sizeof(SkyConst));
   if (e == cudaSuccess) e = cudaMalloc(&p->tw, (size_t)4 * (size_t(1) << kMaxLog2) * 16);
@@ -268,6 +298,7 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_err, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->staged, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->cand_staged, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     free_all(p);
     delete p;
@@ -306,6 +337,7 @@ int fstat_set_data(fstat_plan* p, int det, const void* xh, int dtype, int64_t n,
   p->dtype[det] = dtype;
   p->have[det] = false;
   p->sky_valid = false;
+  p->gtab_valid = false;
   CK(cudaMemcpyAsync(p->xh[det], xh, (size_t)n * eb, cudaMemcpyDefault, st));
   CK(cudaMemsetAsync(p->d_err + 1, 0, sizeof(int), st));
   launch_check_finite(p->xh[det], dtype, n, p->d_err + 1, st);
@@ -313,8 +345,16 @@ int fstat_set_data(fstat_plan* p, int det, const void* xh, int dtype, int64_t n,
   CK(cudaMemcpyAsync(p->h_err + 1, p->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (p->h_err[1] != 0) return p->h_err[1];
-  p->geo.w[det] = 1.0 / (2.0 * sigma * sigma);
+  p->sigma[det] = sigma;
   p->have[det] = true;
+  // common rescaling by the smallest sigma among the detectors with data
+  double ref = 0.0;
+  for (int X = 0; X < p->d.n_det; ++X)
+    if (p->have[X] && (ref == 0.0 || p->sigma[X] < ref)) ref = p->sigma[X];
+  p->sigma_ref = ref;
+  p->geo.inv_sigma_ref = 1.0 / ref;
+  for (int X = 0; X < p->d.n_det; ++X)
+    p->geo.w[X] = p->have[X] ? ref * ref / (2.0 * p->sigma[X] * p->sigma[X]) : 0.0;
   return FSTAT_OK;
 }
 
@@ -359,23 +399,88 @@ int fstat_compute(fstat_plan* p, const fstat_template* tmpl, int64_t n_tmpl, flo
     }
     launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, (int)i, (int)(j - i), p->d_coef, st);
     CK(cudaGetLastError());
+    // Templates alternate between the caller's stream (intermediate Z) and
+    // the plan's side stream (Z2), so pass A of one template overlaps pass B
+    // of the previous one; the side stream joins back before the next sky
+    // position overwrites the per-sky series.
+    const bool two = j - i > 1;
+    if (two) {
+      CK(cudaEventRecord(p->fork, st));
+      CK(cudaStreamWaitEvent(p->side, p->fork, 0));
+    }
     for (int64_t k = i; k < j; ++k) {
       float* out = twoF + (int64_t)ord[k] * nfft;
       const TmplCoef* coef = p->d_coef + k;
+      const bool odd = two && ((k - i) & 1);
+      cudaStream_t s = odd ? p->side : st;
+      void* Zb = odd ? p->Z2 : p->Z;
       EventPair ea{}, eb{};
-      if (p->prof) { ea = get_events(p); cudaEventRecord(ea.a, st); }
-      cudaError_t e = launch_a(p, p->ca, p->va, coef, st);
+      if (p->prof) { ea = get_events(p); cudaEventRecord(ea.a, s); }
+      cudaError_t e = launch_a(p, p->ca, p->va, coef, s, Zb);
       if (e != cudaSuccess) return cuda_status(e);
       if (p->prof) {
-        cudaEventRecord(ea.b, st); p->ev[0].push_back(ea); p->launches[0]++;
-        eb = get_events(p); cudaEventRecord(eb.a, st);
+        cudaEventRecord(ea.b, s); p->ev[0].push_back(ea); p->launches[0]++;
+        eb = get_events(p); cudaEventRecord(eb.a, s);
       }
-      e = launch_b(p, p->cb, p->vb, out, st);
+      e = launch_b(p, p->cb, p->vb, out, s, Zb);
       if (e != cudaSuccess) return cuda_status(e);
-      if (p->prof) { cudaEventRecord(eb.b, st); p->ev[1].push_back(eb); p->launches[1]++; }
+      if (p->prof) { cudaEventRecord(eb.b, s); p->ev[1].push_back(eb); p->launches[1]++; }
+    }
+    if (two) {
+      CK(cudaEventRecord(p->join, p->side));
+      CK(cudaStreamWaitEvent(st, p->join, 0));
     }
     i = j;
   }
+  CK(cudaEventRecord(p->done, st));
+  return FSTAT_OK;
+}
+
+int fstat_grad(fstat_plan* p, const fstat_candidate* cand, int64_t n, float* twoF, float* grad,
+               void* stream) {
+  if (!p || n < 0 || (n > 0 && (!cand || !twoF || !grad)) || n > INT32_MAX) return FSTAT_ERR_INVALID_ARG;
+  for (int X = 0; X < p->d.n_det; ++X)
+    if (!p->have[X]) return FSTAT_ERR_NOT_READY;
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(cand[i].f) || !std::isfinite(cand[i].f1dot) || !std::isfinite(cand[i].alpha) ||
+        !std::isfinite(cand[i].delta) || !std::isfinite(cand[i].f2dot))
+      return FSTAT_ERR_INVALID_ARG;
+  if (n == 0) return FSTAT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!p->gtab) CK(cudaMalloc(&p->gtab, grad_table_bytes(p->d.n_det, p->d.n_samples)));
+  if (!p->gtab_valid) {
+    const void* xh[kMaxDet];
+    for (int X = 0; X < kMaxDet; ++X) xh[X] = p->xh[X];
+    CK(launch_grad_tables(p->geo, xh, p->dtype, p->gtab, st));
+    p->gtab_valid = true;
+  }
+  if (p->cand_pending) { CK(cudaEventSynchronize(p->cand_staged)); p->cand_pending = false; }
+  if (n > p->ccap) {
+    CK(cudaDeviceSynchronize());
+    if (p->h_cand) cudaFreeHost(p->h_cand);
+    if (p->d_cand) cudaFree(p->d_cand);
+    p->h_cand = nullptr;
+    p->d_cand = nullptr;
+    p->ccap = 0;
+    int64_t c = std::max<int64_t>(n, 256);
+    CK(cudaMallocHost(&p->h_cand, c * sizeof(fstat_candidate)));
+    CK(cudaMalloc(&p->d_cand, c * sizeof(fstat_candidate)));
+    p->ccap = c;
+  }
+  const size_t need = grad_scratch_bytes((int)n, p->geo);
+  if (need > p->gscratch_bytes) {
+    CK(cudaDeviceSynchronize());
+    if (p->gscratch) cudaFree(p->gscratch);
+    p->gscratch = nullptr;
+    p->gscratch_bytes = 0;
+    CK(cudaMalloc(&p->gscratch, need));
+    p->gscratch_bytes = need;
+  }
+  std::memcpy(p->h_cand, cand, (size_t)n * sizeof(fstat_candidate));
+  CK(cudaMemcpyAsync(p->d_cand, p->h_cand, (size_t)n * sizeof(fstat_candidate), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(p->cand_staged, st));
+  p->cand_pending = true;
+  CK(launch_grad(p->geo, p->gtab, p->d_cand, (int)n, p->gscratch, twoF, grad, st));
   CK(cudaEventRecord(p->done, st));
   return FSTAT_OK;
 }
@@ -427,10 +532,13 @@ int fstat_export_sky(fstat_plan* p, double alpha, double delta, double* ga, doub
       const double* f = reinterpret_cast<const double*>(buf.data()) + 4 * pos;
       for (int q = 0; q < 4; ++q) v[q] = f[q];
     }
-    if (ga) { ga[2 * j] = v[0]; ga[2 * j + 1] = v[1]; }
-    if (gb) { gb[2 * j] = v[2]; gb[2 * j + 1] = v[3]; }
+    // back to the documented units: G = sum w a z with w = 1/(2 sigma^2)
+    const double g = 1.0 / p->sigma_ref;
+    if (ga) { ga[2 * j] = v[0] * g; ga[2 * j + 1] = v[1] * g; }
+    if (gb) { gb[2 * j] = v[2] * g; gb[2 * j + 1] = v[3] * g; }
   }
-  if (abcd) { abcd[0] = sc.A; abcd[1] = sc.B; abcd[2] = sc.C; abcd[3] = sc.D; }
+  const double g2 = 1.0 / (p->sigma_ref * p->sigma_ref);
+  if (abcd) { abcd[0] = sc.A * g2; abcd[1] = sc.B * g2; abcd[2] = sc.C * g2; abcd[3] = sc.D * g2 * g2; }
   return FSTAT_OK;
 }
 

@@ -81,7 +81,12 @@ __global__ void k_sky_setup(Geo g, double alpha, double delta, SkyConst* out) {
   *out = s;
 }
 
-// Step (iii): z = x_h exp(-i 2 pi frac(f_h t_m(t_k))).
+// Step (iii): z = x_h exp(-i 2 pi frac(f_h t_m(t_k))), stored divided by a
+// common sigma_ref.  Rescaling every detector's series by the same factor,
+// with weights w_X = sigma_ref^2 / (2 sigma_X^2), scales G by sigma_ref and
+// A, B, C by sigma_ref^2, which leaves eq. (Fstat) unchanged while every FP32
+// value stays O(1) whatever the units of x_h (strain-scaled data would
+// overflow 1/(2 sigma^2) and |Fa|^2 in FP32).
 template <typename TIn, typename TZ>
 __global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* __restrict__ z,
                                  const SkyConst* __restrict__ skyp) {
@@ -93,15 +98,16 @@ __global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* _
     double ph = g.f_het * roemer(g, s, X, t, &r);
     ph -= floor(ph);
     TIn x = xh[k];
+    const double is = g.inv_sigma_ref;
     if constexpr (sizeof(TZ) == sizeof(float2)) {
       float sn, cs;
       sincospif(2.0f * (float)ph, &sn, &cs);
-      float xr = (float)x.x, xi = (float)x.y;
+      float xr = (float)((double)x.x * is), xi = (float)((double)x.y * is);
       z[k] = make_float2(xr * cs + xi * sn, xi * cs - xr * sn);
     } else {
       double sn, cs;
       sincospi(2.0 * ph, &sn, &cs);
-      double xr = (double)x.x, xi = (double)x.y;
+      double xr = (double)x.x * is, xi = (double)x.y * is;
       z[k] = make_double2(xr * cs + xi * sn, xi * cs - xr * sn);
     }
   }

@@ -191,3 +191,19 @@ def test_gpu_noise_statistics_chi2_4():
     half, lim = t.n_fft // 2, int(0.4 * t.n_fft)
     s = out[half - lim: half + lim: 2]
     assert abs(s.mean() - 4.0) < 3 * np.sqrt(8.0 / len(s))
+
+
+def test_physical_units_give_the_same_2F():
+    # 2F is invariant under a common rescaling x_X -> c x_X, sigma_X -> c
+    # sigma_X of every detector; strain-scaled data (sigma ~ 1e-23) must not
+    # overflow anywhere in FP32.
+    t = small(seed=18)
+    x = synth.make_data(t)
+    tm = t.templates()
+    ref = run_gpu(t, x, tm)
+    scale = [3e-23, 3e-23]
+    xs = [(x[X].astype(np.complex128) * scale[X]).astype(np.complex64) for X in range(2)]
+    sig = [t.sigmas[X] * scale[X] for X in range(2)]
+    got = run_gpu(t, xs, tm, sigmas=sig)
+    assert np.all(np.isfinite(got))
+    assert_parity(got, ref, rel=1e-4, abs_=1e-3)
