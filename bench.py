@@ -31,7 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import config2, make_noise  # noqa: E402
+from workloads import config2, config3, make_noise  # noqa: E402
 
 METRIC = "templates/s and 2F-bins/s on 1 GB300 at |d2F|<=1e-3·2F+0.02 vs plain FP64-GPU path"
 UNIT = "templates/s"
@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--shape", default="", help="n1,ca,va,cb,vb: fixed FFT split and CTA shapes (skip autotune)")
     return ap.parse_args()
 
 
@@ -142,6 +145,18 @@ def ncu_traffic(kernel: str):
     except (OSError, KeyError, ValueError):
         pass
     return None
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """The slowest rank's number (whole-job time = max over replicas)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    v = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
 
 
 def make_inputs(t, rank):
@@ -236,7 +251,12 @@ def run_ours(args, rank, world, local_rank):
     plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
     for X in range(len(t.detectors)):
         plan.set_data(X, xs[X], t.sigmas[X])
-    plan.autotune(stream)               # plan set-up: pick FFT split and CTA shapes
+    if args.shape:                      # plan set-up: FFT split and CTA shapes
+        n1_, ca, va, cb, vb = (int(v) for v in args.shape.split(","))
+        plan.set_split(n1_)
+        plan.set_cta(ca, cb, va, vb)
+    else:
+        plan.autotune(stream)
     out = torch.empty((chunk, n_fft), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > L2
     chunks = [tm[i:i + chunk] for i in range(0, n_tmpl, chunk)]
@@ -272,10 +292,7 @@ def run_ours(args, rank, world, local_rank):
     ms = sum(a.elapsed_time(b) for a, b in ev)
     stats = {k: plan.kernel_stats(k) for k in (0, 1, 2)}
     plan.set_profiling(False)
-    if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = reduce_max(ms, world, dev)
     total_tmpl = n_tmpl * args.steps * world
     value = total_tmpl / (ms / 1e3)
     launches = args.steps * (len(chunks) + 2 * n_tmpl + 3 + len(t.detectors))
@@ -313,6 +330,14 @@ def run_ours(args, rank, world, local_rank):
                            "l2": "flushed between steps (256 MB write, untimed)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "gpu_launches": launches, "clocks": clocks.summary()}
+
+    # the same step replayed as one CUDA graph (per-sky work + all templates)
+    if rank == 0 and not args.no_graph:
+        line["graph"] = graph_bench(t, xs, tm, chunk, dev, stream, args, flush)
+
+    # batched uneven targets (different spans, bands, FFT lengths) in one graph
+    if rank == 0 and not args.no_uneven:
+        line["uneven_targets"] = uneven_bench(dev, stream)
 
     # FP64-GPU comparison path (same kernels in FP64), timed on a subset
     if rank == 0 and not args.no_fp64:
@@ -361,6 +386,84 @@ def fp64_gpu(t, xs, tm_all, n, dev, stream, mixed_value):
     v = total / ((ms_sky + total * per_t) / 1e3)
     return {"value": v, "unit": UNIT, "sample": f"per-sky step + {n} templates, extrapolated to {total}",
             "mixed_over_fp64": mixed_value / v}
+
+
+def graph_bench(t, xs, tm, chunk, dev, stream, args, flush):
+    """The bench step captured once as a CUDA graph (fstat_batch with an
+    output ring of `chunk` rows) and replayed: same work, no per-kernel host
+    launches and no timing events."""
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+
+    plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
+    for X in range(len(t.detectors)):
+        plan.set_data(X, xs[X], t.sigmas[X])
+    plan.autotune(stream)
+    out = torch.empty((chunk, t.n_fft), dtype=torch.float32, device=dev)
+    batch = pkg.FstatBatch()
+    batch.add(plan, tm, out, out_rows=chunk)
+    batch.instantiate(stream)
+    for _ in range(max(1, args.warmup - 1)):
+        batch.launch(stream)
+    torch.cuda.synchronize(dev)
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        batch.launch(stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms += a.elapsed_time(b)
+    nodes = batch.nodes
+    batch.close()
+    plan.close()
+    return {"value": len(tm) * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "graph_nodes": nodes}
+
+
+def uneven_bench(dev, stream):
+    """Four targets with different spans, bands and FFT lengths (2^18..2^22,
+    561..13333 templates), all in one CUDA graph; seeded noise."""
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+
+    targets = config3()
+    batch = pkg.FstatBatch()
+    plans, keep = [], []
+    n_tmpl = n_bins = 0
+    for tg in targets:
+        xs = [make_noise(tg.seed, X, tg.n_samples, tg.sigmas[X], "c64") for X in range(len(tg.detectors))]
+        plan = pkg.FstatPlan.from_target(tg, pkg.MIXED)
+        for X in range(len(tg.detectors)):
+            plan.set_data(X, xs[X], tg.sigmas[X])
+        plan.autotune(stream)
+        out = torch.empty((64, tg.n_fft), dtype=torch.float32, device=dev)
+        tm = tg.templates()
+        batch.add(plan, tm, out, out_rows=64)
+        plans.append(plan)
+        keep.append(out)
+        n_tmpl += len(tm)
+        n_bins += len(tm) * tg.n_fft
+    batch.instantiate(stream)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    batch.launch(stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b)
+    nodes = batch.nodes
+    batch.close()
+    for p in plans:
+        p.close()
+    return {"value": n_tmpl / (ms / 1e3), "unit": UNIT, "bins_per_s": n_bins / (ms / 1e3),
+            "targets": [{"n_samples": tg.n_samples, "n_fft": tg.n_fft, "templates": tg.n_templates,
+                         "f_het": tg.f_het} for tg in targets],
+            "ms": ms, "graph_nodes": nodes}
 
 
 def refine_bench(t, xs, dev, n_cand=4096, steps=20):

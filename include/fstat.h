@@ -214,6 +214,31 @@ int fstat_twoF_noalloc(const void* g_pairs, int64_t n_samples, int64_t n_fft, do
                        double A, double B, double C, double f1dot, double f2dot, float* twoF,
                        void* stream);
 
+/* Batch: several plans' template banks (uneven targets: different sample
+ * counts, spans and FFT lengths) captured once into one CUDA graph and
+ * replayed with one launch.  Each added plan's work runs on its own branch
+ * of the graph (per-sky work, spindown coefficients, FFT passes; the
+ * template loop of Sec. 3 repeated over targets), so small targets fill the
+ * GPU alongside large ones.
+ *   fstat_batch_add: `tmpl` (HOST, n templates) is copied; `twoF` (DEVICE)
+ *     receives row (i mod out_rows) for template i (out_rows = 0 -> n, one
+ *     row per template; a smaller ring lets a consumer stream results).  One
+ *     entry per plan.  The plan must have its data set.
+ *   fstat_batch_instantiate: copies the banks to the device, runs them once
+ *     on `stream` (synchronous), captures the graph.  Plans must stay alive
+ *     and unmodified (data, split, CTA shapes) while the batch is used.
+ *   fstat_batch_launch: replays every entry on `stream` (asynchronous);
+ *     per-sky work is always redone.  fstat_batch_nodes: graph node count.
+ * Errors: INVALID_ARG, NOT_READY, OOM, CUDA. */
+typedef struct fstat_batch fstat_batch;
+int fstat_batch_create(fstat_batch** out);
+int fstat_batch_add(fstat_batch* batch, fstat_plan* plan, const fstat_template* tmpl, int64_t n,
+                    float* twoF, int64_t out_rows);
+int fstat_batch_instantiate(fstat_batch* batch, void* stream);
+int fstat_batch_launch(fstat_batch* batch, void* stream);
+int fstat_batch_nodes(const fstat_batch* batch, int64_t* nodes);
+void fstat_batch_destroy(fstat_batch* batch);
+
 void fstat_plan_destroy(fstat_plan* plan);
 const char* fstat_strerror(int code);
 

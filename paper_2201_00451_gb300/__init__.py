@@ -42,7 +42,8 @@ EXPORTS = (
     "fstat_invalidate_sky", "fstat_export_sky", "fstat_sync", "fstat_set_profiling",
     "fstat_kernel_stats", "fstat_get_split", "fstat_set_split", "fstat_plan_destroy",
     "fstat_strerror", "fstat_twoF_noalloc", "fstat_get_cta", "fstat_set_cta", "fstat_autotune",
-    "fstat_grad",
+    "fstat_grad", "fstat_batch_create", "fstat_batch_add", "fstat_batch_instantiate",
+    "fstat_batch_launch", "fstat_batch_nodes", "fstat_batch_destroy",
 )
 
 
@@ -117,6 +118,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fstat_set_cta": (i32, [P, i32, i32, i32, i32]),
         "fstat_autotune": (i32, [P, P]),
         "fstat_grad": (i32, [P, P, i64, P, P, P]),
+        "fstat_batch_create": (i32, [ctypes.POINTER(P)]),
+        "fstat_batch_add": (i32, [P, P, P, i64, P, i64]),
+        "fstat_batch_instantiate": (i32, [P, P]),
+        "fstat_batch_launch": (i32, [P, P]),
+        "fstat_batch_nodes": (i32, [P, ctypes.POINTER(i64)]),
+        "fstat_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -324,3 +331,49 @@ class FstatPlan:
     def autotune(self, stream=None):
         """fstat_autotune: pick the fastest FFT split and CTA shapes."""
         _check(self._lib.fstat_autotune(self._p, _stream_handle(stream)), "fstat_autotune")
+
+
+class FstatBatch:
+    """fstat_batch_*: several plans' template banks replayed as one CUDA graph."""
+
+    def __init__(self):
+        self._lib = load()
+        self._b = ctypes.c_void_p()
+        _check(self._lib.fstat_batch_create(ctypes.byref(self._b)), "fstat_batch_create")
+        self._keep = []
+
+    def add(self, plan: FstatPlan, templates, out, out_rows: int = 0):
+        t = as_templates(templates)
+        rc = self._lib.fstat_batch_add(self._b, plan._p, ctypes.c_void_p(t.ctypes.data), len(t),
+                                       ctypes.c_void_p(out.data_ptr()), int(out_rows))
+        _check(rc, "fstat_batch_add")
+        self._keep.append((plan, out))
+
+    def instantiate(self, stream=None):
+        _check(self._lib.fstat_batch_instantiate(self._b, _stream_handle(stream)), "fstat_batch_instantiate")
+
+    def launch(self, stream=None):
+        _check(self._lib.fstat_batch_launch(self._b, _stream_handle(stream)), "fstat_batch_launch")
+
+    @property
+    def nodes(self) -> int:
+        n = ctypes.c_int64()
+        _check(self._lib.fstat_batch_nodes(self._b, ctypes.byref(n)), "fstat_batch_nodes")
+        return n.value
+
+    def close(self):
+        if self._b:
+            self._lib.fstat_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

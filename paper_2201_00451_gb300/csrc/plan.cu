@@ -358,73 +358,54 @@ int fstat_set_data(fstat_plan* p, int det, const void* xh, int dtype, int64_t n,
   return FSTAT_OK;
 }
 
-int fstat_compute(fstat_plan* p, const fstat_template* tmpl, int64_t n_tmpl, float* twoF,
-                  void* stream) {
-  if (!p || n_tmpl < 0 || (n_tmpl > 0 && (!tmpl || !twoF))) return FSTAT_ERR_INVALID_ARG;
-  if (n_tmpl > INT32_MAX) return FSTAT_ERR_INVALID_ARG;
-  for (int X = 0; X < p->d.n_det; ++X)
-    if (!p->have[X]) return FSTAT_ERR_NOT_READY;
-  for (int64_t i = 0; i < n_tmpl; ++i)
-    if (!std::isfinite(tmpl[i].alpha) || !std::isfinite(tmpl[i].delta) ||
-        !std::isfinite(tmpl[i].f1dot) || !std::isfinite(tmpl[i].f2dot))
-      return FSTAT_ERR_INVALID_ARG;
-  if (n_tmpl == 0) return FSTAT_OK;
-  cudaStream_t st = (cudaStream_t)stream;
-  int rc = ensure_capacity(p, n_tmpl);
-  if (rc) return rc;
-  if (p->staged_pending) { CK(cudaEventSynchronize(p->staged)); p->staged_pending = false; }
+}  // extern "C"
 
-  std::memcpy(p->h_tmpl, tmpl, (size_t)n_tmpl * sizeof(fstat_template));
-  int* ord = p->h_order;
-  std::iota(ord, ord + n_tmpl, 0);
-  std::stable_sort(ord, ord + n_tmpl, [&](int a, int b) {
-    if (tmpl[a].alpha != tmpl[b].alpha) return tmpl[a].alpha < tmpl[b].alpha;
-    return tmpl[a].delta < tmpl[b].delta;
-  });
-  CK(cudaMemcpyAsync(p->d_tmpl, p->h_tmpl, (size_t)n_tmpl * sizeof(fstat_template),
-                     cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(p->d_order, p->h_order, (size_t)n_tmpl * sizeof(int), cudaMemcpyHostToDevice, st));
-  CK(cudaEventRecord(p->staged, st));
-  p->staged_pending = true;
+namespace {
 
+// Enqueue steps (iii)-(vii) for n templates on `st`.  h_tmpl/h_ord (host)
+// give the sky grouping; d_tmpl/d_ord/d_coef are the device copies the
+// kernels read.  force_sky: always redo the per-sky work (graph capture).
+int enqueue_compute(fstat_plan* p, const fstat_template* h_tmpl, const int* h_ord, int64_t n,
+                    const fstat_template* d_tmpl, const int* d_ord, TmplCoef* d_coef, float* twoF,
+                    int64_t out_rows, cudaStream_t st, bool force_sky, bool prof) {
   const int64_t nfft = p->d.n_fft;
   int64_t i = 0;
-  while (i < n_tmpl) {
-    const fstat_template& t0 = tmpl[ord[i]];
+  while (i < n) {
+    const fstat_template& t0 = h_tmpl[h_ord[i]];
     int64_t j = i + 1;
-    while (j < n_tmpl && tmpl[ord[j]].alpha == t0.alpha && tmpl[ord[j]].delta == t0.delta) ++j;
-    if (!(p->sky_valid && p->sky_alpha == t0.alpha && p->sky_delta == t0.delta)) {
-      rc = run_sky(p, t0.alpha, t0.delta, st);
+    while (j < n && h_tmpl[h_ord[j]].alpha == t0.alpha && h_tmpl[h_ord[j]].delta == t0.delta) ++j;
+    if (force_sky || !(p->sky_valid && p->sky_alpha == t0.alpha && p->sky_delta == t0.delta)) {
+      int rc = run_sky(p, t0.alpha, t0.delta, st);
       if (rc) return rc;
     }
-    launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, (int)i, (int)(j - i), p->d_coef, st);
+    launch_tmpl_coef(p->sky, p->d.dt, d_tmpl, d_ord, (int)i, (int)(j - i), d_coef, st);
     CK(cudaGetLastError());
-    // Templates alternate between the caller's stream (intermediate Z) and
-    // the plan's side stream (Z2), so pass A of one template overlaps pass B
-    // of the previous one; the side stream joins back before the next sky
-    // position overwrites the per-sky series.
+    // Templates alternate between `st` (intermediate Z) and the plan's side
+    // stream (Z2), so pass A of one template overlaps pass B of the previous
+    // one; the side stream joins back before the next sky position
+    // overwrites the per-sky series.
     const bool two = j - i > 1;
     if (two) {
       CK(cudaEventRecord(p->fork, st));
       CK(cudaStreamWaitEvent(p->side, p->fork, 0));
     }
     for (int64_t k = i; k < j; ++k) {
-      float* out = twoF + (int64_t)ord[k] * nfft;
-      const TmplCoef* coef = p->d_coef + k;
+      float* out = twoF + ((int64_t)h_ord[k] % out_rows) * nfft;
+      const TmplCoef* coef = d_coef + k;
       const bool odd = two && ((k - i) & 1);
       cudaStream_t s = odd ? p->side : st;
       void* Zb = odd ? p->Z2 : p->Z;
       EventPair ea{}, eb{};
-      if (p->prof) { ea = get_events(p); cudaEventRecord(ea.a, s); }
+      if (prof) { ea = get_events(p); cudaEventRecord(ea.a, s); }
       cudaError_t e = launch_a(p, p->ca, p->va, coef, s, Zb);
       if (e != cudaSuccess) return cuda_status(e);
-      if (p->prof) {
+      if (prof) {
         cudaEventRecord(ea.b, s); p->ev[0].push_back(ea); p->launches[0]++;
         eb = get_events(p); cudaEventRecord(eb.a, s);
       }
       e = launch_b(p, p->cb, p->vb, out, s, Zb);
       if (e != cudaSuccess) return cuda_status(e);
-      if (p->prof) { cudaEventRecord(eb.b, s); p->ev[1].push_back(eb); p->launches[1]++; }
+      if (prof) { cudaEventRecord(eb.b, s); p->ev[1].push_back(eb); p->launches[1]++; }
     }
     if (two) {
       CK(cudaEventRecord(p->join, p->side));
@@ -432,6 +413,52 @@ int fstat_compute(fstat_plan* p, const fstat_template* tmpl, int64_t n_tmpl, flo
     }
     i = j;
   }
+  return FSTAT_OK;
+}
+
+int validate_templates(const fstat_plan* p, const fstat_template* tmpl, int64_t n) {
+  if (n < 0 || (n > 0 && !tmpl) || n > INT32_MAX) return FSTAT_ERR_INVALID_ARG;
+  for (int X = 0; X < p->d.n_det; ++X)
+    if (!p->have[X]) return FSTAT_ERR_NOT_READY;
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(tmpl[i].alpha) || !std::isfinite(tmpl[i].delta) ||
+        !std::isfinite(tmpl[i].f1dot) || !std::isfinite(tmpl[i].f2dot))
+      return FSTAT_ERR_INVALID_ARG;
+  return FSTAT_OK;
+}
+
+void sky_order(const fstat_template* tmpl, int64_t n, int* ord) {
+  std::iota(ord, ord + n, 0);
+  std::stable_sort(ord, ord + n, [&](int a, int b) {
+    if (tmpl[a].alpha != tmpl[b].alpha) return tmpl[a].alpha < tmpl[b].alpha;
+    return tmpl[a].delta < tmpl[b].delta;
+  });
+}
+
+}  // namespace
+
+extern "C" {
+
+int fstat_compute(fstat_plan* p, const fstat_template* tmpl, int64_t n_tmpl, float* twoF,
+                  void* stream) {
+  if (!p || (n_tmpl > 0 && !twoF)) return FSTAT_ERR_INVALID_ARG;
+  int rc = validate_templates(p, tmpl, n_tmpl);
+  if (rc) return rc;
+  if (n_tmpl == 0) return FSTAT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = ensure_capacity(p, n_tmpl);
+  if (rc) return rc;
+  if (p->staged_pending) { CK(cudaEventSynchronize(p->staged)); p->staged_pending = false; }
+  std::memcpy(p->h_tmpl, tmpl, (size_t)n_tmpl * sizeof(fstat_template));
+  sky_order(tmpl, n_tmpl, p->h_order);
+  CK(cudaMemcpyAsync(p->d_tmpl, p->h_tmpl, (size_t)n_tmpl * sizeof(fstat_template),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(p->d_order, p->h_order, (size_t)n_tmpl * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(p->staged, st));
+  p->staged_pending = true;
+  rc = enqueue_compute(p, tmpl, p->h_order, n_tmpl, p->d_tmpl, p->d_order, p->d_coef, twoF, n_tmpl, st,
+                       false, p->prof);
+  if (rc) return rc;
   CK(cudaEventRecord(p->done, st));
   return FSTAT_OK;
 }
@@ -739,3 +766,151 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
   save_tune(key, best);
   return FSTAT_OK;
 }
+
+// ------------------------------------------------------------------- batch
+struct BatchEntry {
+  fstat_plan* p = nullptr;
+  std::vector<fstat_template> tmpl;
+  std::vector<int> ord;
+  float* twoF = nullptr;
+  int64_t out_rows = 0;
+  fstat_template* d_tmpl = nullptr;
+  int* d_ord = nullptr;
+  TmplCoef* d_coef = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+struct fstat_batch {
+  std::vector<BatchEntry> e;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  size_t nodes = 0;
+};
+
+namespace {
+
+void batch_release(fstat_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  for (auto& x : b->e) {
+    if (x.d_tmpl) cudaFree(x.d_tmpl);
+    if (x.d_ord) cudaFree(x.d_ord);
+    if (x.d_coef) cudaFree(x.d_coef);
+    if (x.s) cudaStreamDestroy(x.s);
+    if (x.fork) cudaEventDestroy(x.fork);
+    if (x.join) cudaEventDestroy(x.join);
+    x.d_tmpl = nullptr; x.d_ord = nullptr; x.d_coef = nullptr;
+    x.s = nullptr; x.fork = nullptr; x.join = nullptr;
+  }
+  if (b->cap) cudaStreamDestroy(b->cap);
+  b->cap = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fstat_batch_create(fstat_batch** out) {
+  if (!out) return FSTAT_ERR_INVALID_ARG;
+  *out = new (std::nothrow) fstat_batch();
+  return *out ? FSTAT_OK : FSTAT_ERR_OOM;
+}
+
+int fstat_batch_add(fstat_batch* b, fstat_plan* p, const fstat_template* tmpl, int64_t n, float* twoF,
+                    int64_t out_rows) {
+  if (!b || !p || n < 1 || !twoF || out_rows < 0 || b->exec) return FSTAT_ERR_INVALID_ARG;
+  for (auto& x : b->e)
+    if (x.p == p) return FSTAT_ERR_INVALID_ARG;  // one entry per plan (shared buffers)
+  int rc = validate_templates(p, tmpl, n);
+  if (rc) return rc;
+  BatchEntry x;
+  x.p = p;
+  x.tmpl.assign(tmpl, tmpl + n);
+  x.ord.resize(n);
+  sky_order(tmpl, n, x.ord.data());
+  x.twoF = twoF;
+  x.out_rows = out_rows ? out_rows : n;
+  b->e.push_back(std::move(x));
+  return FSTAT_OK;
+}
+
+int fstat_batch_instantiate(fstat_batch* b, void* stream) {
+  if (!b || b->e.empty() || b->exec) return FSTAT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = FSTAT_OK;
+  auto fail = [&](int code) { batch_release(b); return code; };
+  for (auto& x : b->e) {
+    const int64_t n = (int64_t)x.tmpl.size();
+    if (cudaMalloc(&x.d_tmpl, n * sizeof(fstat_template)) != cudaSuccess ||
+        cudaMalloc(&x.d_ord, n * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&x.d_coef, n * sizeof(TmplCoef)) != cudaSuccess)
+      return fail(FSTAT_ERR_OOM);
+    if (cudaMemcpy(x.d_tmpl, x.tmpl.data(), n * sizeof(fstat_template), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(x.d_ord, x.ord.data(), n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(FSTAT_ERR_CUDA);
+    if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess)
+      return fail(FSTAT_ERR_CUDA);
+    // one ordinary run first: sets kernel attributes outside the capture
+    rc = enqueue_compute(x.p, x.tmpl.data(), x.ord.data(), n, x.d_tmpl, x.d_ord, x.d_coef, x.twoF, x.out_rows,
+                         st, true, false);
+    if (rc) return fail(rc);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(FSTAT_ERR_CUDA);
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(FSTAT_ERR_CUDA);
+  std::vector<bool> prof;
+  for (auto& x : b->e) { prof.push_back(x.p->prof); x.p->prof = false; }  // no timing events in the graph
+  if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(FSTAT_ERR_CUDA);
+  for (auto& x : b->e) {
+    cudaEventRecord(x.fork, b->cap);
+    cudaStreamWaitEvent(x.s, x.fork, 0);
+    rc = enqueue_compute(x.p, x.tmpl.data(), x.ord.data(), (int64_t)x.tmpl.size(), x.d_tmpl, x.d_ord, x.d_coef,
+                         x.twoF, x.out_rows, x.s, true, false);
+    if (rc) break;
+    cudaEventRecord(x.join, x.s);
+    cudaStreamWaitEvent(b->cap, x.join, 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  for (size_t k = 0; k < b->e.size(); ++k) b->e[k].p->prof = prof[k];
+  if (rc || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return fail(rc ? rc : FSTAT_ERR_CUDA);
+  }
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return fail(FSTAT_ERR_CUDA);
+  cudaGraphGetNodes(b->graph, nullptr, &b->nodes);
+  for (auto& x : b->e) x.p->sky_valid = false;
+  return FSTAT_OK;
+}
+
+int fstat_batch_launch(fstat_batch* b, void* stream) {
+  if (!b || !b->exec) return FSTAT_ERR_INVALID_ARG;
+  CK(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  for (auto& x : b->e) {
+    x.p->sky_valid = false;
+    CK(cudaEventRecord(x.p->done, (cudaStream_t)stream));
+  }
+  return FSTAT_OK;
+}
+
+int fstat_batch_nodes(const fstat_batch* b, int64_t* nodes) {
+  if (!b || !nodes) return FSTAT_ERR_INVALID_ARG;
+  *nodes = (int64_t)b->nodes;
+  return FSTAT_OK;
+}
+
+void fstat_batch_destroy(fstat_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  batch_release(b);
+  delete b;
+}
+
+}  // extern "C"
