@@ -31,7 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import config2, config3, make_noise  # noqa: E402
+from workloads import config2, config3, config5, make_noise  # noqa: E402
 
 METRIC = "templates/s and 2F-bins/s on 1 GB300 at |d2F|<=1e-3·2F+0.02 vs plain FP64-GPU path"
 UNIT = "templates/s"
@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--streams", type=int, default=2, help="template streams per plan (1..4)")
     ap.add_argument("--shape", default="", help="n1,ca,va,cb,vb: fixed FFT split and CTA shapes (skip autotune)")
     return ap.parse_args()
 
@@ -251,6 +253,7 @@ def run_ours(args, rank, world, local_rank):
     plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
     for X in range(len(t.detectors)):
         plan.set_data(X, xs[X], t.sigmas[X])
+    plan.set_streams(args.streams)
     if args.shape:                      # plan set-up: FFT split and CTA shapes
         n1_, ca, va, cb, vb = (int(v) for v in args.shape.split(","))
         plan.set_split(n1_)
@@ -326,6 +329,7 @@ def run_ours(args, rank, world, local_rank):
                 "bins_per_s": value * n_fft,
                 "tau_F_eff_s": 1.0 / (value * n_fft * len(t.detectors)),
                 "config": {"workload": WORKLOAD, "templates_per_step": n_tmpl, "chunk": chunk,
+                           "streams": args.streams,
                            "precision": "mixed: FP64 timing and phases, FP32 resample/FFT/2F",
                            "l2": "flushed between steps (256 MB write, untimed)",
                            "parallelism": f"replicas x{world}"},
@@ -338,6 +342,10 @@ def run_ours(args, rank, world, local_rank):
     # batched uneven targets (different spans, bands, FFT lengths) in one graph
     if rank == 0 and not args.no_uneven:
         line["uneven_targets"] = uneven_bench(dev, stream)
+
+    # large search (120 d, FFT 2^24, 64 skies x 16384 spindowns): a bounded slice
+    if rank == 0 and not args.no_large:
+        line["large_search"] = large_bench(dev, stream)
 
     # FP64-GPU comparison path (same kernels in FP64), timed on a subset
     if rank == 0 and not args.no_fp64:
@@ -464,6 +472,44 @@ def uneven_bench(dev, stream):
             "targets": [{"n_samples": tg.n_samples, "n_fft": tg.n_fft, "templates": tg.n_templates,
                          "f_het": tg.f_het} for tg in targets],
             "ms": ms, "graph_nodes": nodes}
+
+
+def large_bench(dev, stream, n_tmpl=2048):
+    """The 120-day, 2^24-bin search timed on one sky position: per-sky work
+    once plus n_tmpl spindown templates, extrapolated to the full bank of
+    64 skies x 16 384 templates (per-sky work counted 64 times)."""
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+
+    t = config5()
+    xs = [make_noise(t.seed, X, t.n_samples, t.sigmas[X], "c64") for X in range(len(t.detectors))]
+    plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
+    for X in range(len(t.detectors)):
+        plan.set_data(X, xs[X], t.sigmas[X])
+    plan.autotune(stream)
+    tm = pkg.as_templates(t.templates()[:n_tmpl])
+    out = torch.empty((64, t.n_fft), dtype=torch.float32, device=dev)
+    chunks = [tm[i:i + 64] for i in range(0, len(tm), 64)]
+    plan.compute_ptr(chunks[0][:2], out.data_ptr(), stream)
+    plan.sync()
+    plan.set_profiling(True)
+    plan.invalidate_sky()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for c in chunks:
+        plan.compute_ptr(c, out.data_ptr(), stream)
+    b.record(stream)
+    plan.sync()
+    ms = a.elapsed_time(b)
+    _, ms_sky = plan.kernel_stats(2)
+    plan.close()
+    per_t = (ms - ms_sky) / len(tm)
+    total = t.n_templates
+    job_s = (len(t.skies) * ms_sky + total * per_t) / 1e3
+    return {"value": total / job_s, "unit": UNIT, "bins_per_s": total * t.n_fft / job_s,
+            "sample": f"1 sky: per-sky work {ms_sky:.2f} ms + {len(tm)} templates at {per_t * 1e3:.1f} us each",
+            "job_hours": job_s / 3600.0, "n_fft": t.n_fft, "n_samples": t.n_samples}
 
 
 def refine_bench(t, xs, dev, n_cand=4096, steps=20):

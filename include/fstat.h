@@ -180,6 +180,12 @@ int fstat_set_split(fstat_plan* plan, int64_t n1);
 int fstat_get_cta(const fstat_plan* plan, int* ca, int* va, int* cb, int* vb);
 int fstat_set_cta(fstat_plan* plan, int ca, int va, int cb, int vb);
 
+/* Number of streams (1..4, default 2) over which consecutive templates
+ * rotate inside fstat_compute; each stream owns an n_fft-point intermediate
+ * (16 B per point in FP32), so the FFT passes of consecutive templates
+ * overlap.  Synchronises. */
+int fstat_set_streams(fstat_plan* plan, int n);
+
 /* Autotuner: times every compiled (split, ca, va, cb, vb) for this plan's n_fft on
  * the current data with CUDA events on `stream` and keeps the fastest.
  * Results are cached per (GPU name, n_samples, n_fft, precision, n_det) in

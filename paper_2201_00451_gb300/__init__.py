@@ -43,7 +43,7 @@ EXPORTS = (
     "fstat_kernel_stats", "fstat_get_split", "fstat_set_split", "fstat_plan_destroy",
     "fstat_strerror", "fstat_twoF_noalloc", "fstat_get_cta", "fstat_set_cta", "fstat_autotune",
     "fstat_grad", "fstat_batch_create", "fstat_batch_add", "fstat_batch_instantiate",
-    "fstat_batch_launch", "fstat_batch_nodes", "fstat_batch_destroy",
+    "fstat_batch_launch", "fstat_batch_nodes", "fstat_batch_destroy", "fstat_set_streams",
 )
 
 
@@ -124,6 +124,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fstat_batch_launch": (i32, [P, P]),
         "fstat_batch_nodes": (i32, [P, ctypes.POINTER(i64)]),
         "fstat_batch_destroy": (None, [P]),
+        "fstat_set_streams": (i32, [P, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -327,6 +328,10 @@ class FstatPlan:
 
     def set_cta(self, ca: int, cb: int, va: int = 0, vb: int = 0):
         _check(self._lib.fstat_set_cta(self._p, int(ca), int(va), int(cb), int(vb)), "fstat_set_cta")
+
+    def set_streams(self, n: int):
+        """fstat_set_streams: templates rotate over n streams (1..4)."""
+        _check(self._lib.fstat_set_streams(self._p, int(n)), "fstat_set_streams")
 
     def autotune(self, stream=None):
         """fstat_autotune: pick the fastest FFT split and CTA shapes."""

@@ -205,10 +205,17 @@ k_partial(Geo g, SampleTabs tab, const CandConst* __restrict__ cc, int n_cand, i
   int cnt = 0;
 #pragma unroll
   for (int q = 0; q < kAcc; ++q) inner[q] = 0.f;
-  for (int64_t i = beg + lane; i < end; i += 32) {
-    const int X = (int)(i / g.n);
-    const int64_t k = i - (int64_t)X * g.n;
-    const float w = (float)g.w[X];
+  // detector X and sample k of index i, advanced incrementally (no 64-bit
+  // division, no double->float conversion per sample)
+  int X = (int)((beg + lane) / g.n);
+  int k = (int)(beg + lane - (int64_t)X * g.n);
+  float w = X < g.n_det ? (float)g.w[X] : 0.f;
+  for (int64_t i = beg + lane; i < end; i += 32, k += 32) {
+    while (k >= g.n) {
+      k -= (int)g.n;
+      ++X;
+      w = (float)g.w[X];
+    }
     const float4 r4 = __ldg(&tab.rc[i]);
     const float2 rz = __ldg(&tab.rcz[i]);
     const float4 d0 = __ldg(&tab.d0[i]);

@@ -117,29 +117,6 @@ template <typename PM> __device__ __forceinline__ void cp_pair(PM* dst, const PM
   if constexpr (sizeof(PM) == 32) cp_async16((char*)dst + 16, (const char*)src + 16);
 }
 
-// L2 residency hints: the per-sky series G is read by every template of a
-// sky (keep it: evict_last); a row of the intermediate is dead once pass B
-// has read it (evict_first).
-__device__ __forceinline__ uint64_t l2_evict_last() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
-  return pol;
-}
-__device__ __forceinline__ uint64_t l2_evict_first() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
-  return pol;
-}
-__device__ __forceinline__ void cp_async16_hint(void* smem, const void* gmem, uint64_t pol) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "l"(pol)
-               : "memory");
-}
-template <typename PM> __device__ __forceinline__ void cp_pair_hint(PM* dst, const PM* src, uint64_t pol) {
-  cp_async16_hint(dst, src, pol);
-  if constexpr (sizeof(PM) == 32) cp_async16_hint((char*)dst + 16, (const char*)src + 16, pol);
-}
-
 __device__ __forceinline__ int pad_idx(int pos, int ps) { return pos + (pos >> ps); }
 
 template <typename TW> __device__ __forceinline__ TW tw_ld(const TW* p) { return __ldg(p); }
@@ -411,14 +388,13 @@ k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int
   } else {
     const int n_tiles = n1 / CA;
     auto stage = [&](int it) { return smem + (B::NBUF == 2 ? (it & 1) : 0) * (CA * S::LP) + c * S::LP; };
-    const uint64_t keep = l2_evict_last();
     auto prefetch = [&](int tile, PM* dst) {
       const int col = tile * CA + c;
       const PM* gcol = G + (int64_t)col * lc;
 #pragma unroll
       for (int s = 0; s < S::R0; ++s) {
         const int n2 = t + s * S::TPC;
-        if (col + n1 * n2 < n) cp_pair_hint(dst + pad_idx(n2, S::PS), gcol + n2, keep);
+        if (col + n1 * n2 < n) cp_pair(dst + pad_idx(n2, S::PS), gcol + n2);
       }
     };
     int tile = blockIdx.x;
@@ -500,13 +476,12 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
   } else {
     const int n_tiles = n2 / CB;
     auto stage = [&](int it) { return smem + (B::NBUF == 2 ? (it & 1) : 0) * (CB * S::LP) + c; };
-    const uint64_t drop = l2_evict_first();
     auto prefetch = [&](int tile, PM* dst) {
       const int k2 = tile * CB + c;
 #pragma unroll
       for (int s = 0; s < S::R0; ++s) {
         const int n1 = t + s * S::TPC;
-        cp_pair_hint(dst + pad_idx(n1, S::PS) * CB, Z + (int64_t)n1 * n2 + k2, drop);
+        cp_pair(dst + pad_idx(n1, S::PS) * CB, Z + (int64_t)n1 * n2 + k2);
       }
     };
     int tile = blockIdx.x;

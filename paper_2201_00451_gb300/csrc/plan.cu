@@ -42,9 +42,15 @@ struct fstat_plan {
   void* z = nullptr;
   void* G = nullptr;
   void* Z = nullptr;
-  void* Z2 = nullptr;              // second intermediate: template pairs overlap on two streams
-  cudaStream_t side = nullptr;     // plan-owned stream for every other template
-  cudaEvent_t fork = nullptr, join = nullptr;
+  // templates rotate over nstream streams (the caller's + plan-owned side
+  // streams), each with its own intermediate, so FFT passes of consecutive
+  // templates overlap
+  static constexpr int kMaxStreams = 4;
+  int nstream = 2;
+  void* Zs[kMaxStreams] = {};      // Zs[0] aliases Z
+  cudaStream_t side[kMaxStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kMaxStreams] = {};
   double* partials = nullptr;
   int nblk = 0;
   SkyConst* sky = nullptr;
@@ -108,10 +114,12 @@ void free_all(fstat_plan* p) {
   if (p->z) cudaFree(p->z);
   if (p->G) cudaFree(p->G);
   if (p->Z) cudaFree(p->Z);
-  if (p->Z2) cudaFree(p->Z2);
-  if (p->side) cudaStreamDestroy(p->side);
+  for (int k = 1; k < fstat_plan::kMaxStreams; ++k) {
+    if (p->Zs[k]) cudaFree(p->Zs[k]);
+    if (p->side[k]) cudaStreamDestroy(p->side[k]);
+    if (p->join[k]) cudaEventDestroy(p->join[k]);
+  }
   if (p->fork) cudaEventDestroy(p->fork);
-  if (p->join) cudaEventDestroy(p->join);
   if (p->partials) cudaFree(p->partials);
   if (p->sky) cudaFree(p->sky);
   if (p->tw) cudaFree(p->tw);
@@ -286,10 +294,13 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   if (e == cudaSuccess) e = cudaMalloc(&p->z, (size_t)d.n_det * N * zb);
   if (e == cudaSuccess) e = cudaMalloc(&p->G, (size_t)(N + (int64_t(1) << kMaxLog2)) * p->pair_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->Z, (size_t)d.n_fft * p->pair_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&p->Z2, (size_t)d.n_fft * p->pair_bytes);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming);
+  p->Zs[0] = p->Z;
+  for (int k = 1; k < p->nstream && e == cudaSuccess; ++k) {
+    e = cudaMalloc(&p->Zs[k], (size_t)d.n_fft * p->pair_bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join[k], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&p->partials, (size_t)3 * p->nblk * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->sky, sizeof(SkyConst));
   if (e == cudaSuccess) e = cudaMalloc(&p->tw, (size_t)4 * (size_t(1) << kMaxLog2) * 16);
@@ -380,21 +391,21 @@ int enqueue_compute(fstat_plan* p, const fstat_template* h_tmpl, const int* h_or
     }
     launch_tmpl_coef(p->sky, p->d.dt, d_tmpl, d_ord, (int)i, (int)(j - i), d_coef, st);
     CK(cudaGetLastError());
-    // Templates alternate between `st` (intermediate Z) and the plan's side
-    // stream (Z2), so pass A of one template overlaps pass B of the previous
-    // one; the side stream joins back before the next sky position
-    // overwrites the per-sky series.
-    const bool two = j - i > 1;
-    if (two) {
+    // Templates rotate over `st` and the plan's side streams, each with its
+    // own intermediate, so the passes of consecutive templates overlap; the
+    // side streams join back before the next sky position overwrites the
+    // per-sky series.
+    const int ns = (int)std::min<int64_t>(p->nstream, j - i);
+    if (ns > 1) {
       CK(cudaEventRecord(p->fork, st));
-      CK(cudaStreamWaitEvent(p->side, p->fork, 0));
+      for (int q = 1; q < ns; ++q) CK(cudaStreamWaitEvent(p->side[q], p->fork, 0));
     }
     for (int64_t k = i; k < j; ++k) {
       float* out = twoF + ((int64_t)h_ord[k] % out_rows) * nfft;
       const TmplCoef* coef = d_coef + k;
-      const bool odd = two && ((k - i) & 1);
-      cudaStream_t s = odd ? p->side : st;
-      void* Zb = odd ? p->Z2 : p->Z;
+      const int q = (int)((k - i) % ns);
+      cudaStream_t s = q ? p->side[q] : st;
+      void* Zb = p->Zs[q];
       EventPair ea{}, eb{};
       if (prof) { ea = get_events(p); cudaEventRecord(ea.a, s); }
       cudaError_t e = launch_a(p, p->ca, p->va, coef, s, Zb);
@@ -407,9 +418,9 @@ int enqueue_compute(fstat_plan* p, const fstat_template* h_tmpl, const int* h_or
       if (e != cudaSuccess) return cuda_status(e);
       if (prof) { cudaEventRecord(eb.b, s); p->ev[1].push_back(eb); p->launches[1]++; }
     }
-    if (two) {
-      CK(cudaEventRecord(p->join, p->side));
-      CK(cudaStreamWaitEvent(st, p->join, 0));
+    for (int q = 1; q < ns; ++q) {
+      CK(cudaEventRecord(p->join[q], p->side[q]));
+      CK(cudaStreamWaitEvent(st, p->join[q], 0));
     }
     i = j;
   }
@@ -610,6 +621,18 @@ int fstat_set_split(fstat_plan* p, int64_t n1) {
   return set_split(p, l);
 }
 
+int fstat_set_streams(fstat_plan* p, int n) {
+  if (!p || n < 1 || n > fstat_plan::kMaxStreams) return FSTAT_ERR_INVALID_ARG;
+  CK(cudaDeviceSynchronize());
+  for (int k = 1; k < n; ++k) {
+    if (!p->Zs[k]) CK(cudaMalloc(&p->Zs[k], (size_t)p->d.n_fft * p->pair_bytes));
+    if (!p->side[k]) CK(cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking));
+    if (!p->join[k]) CK(cudaEventCreateWithFlags(&p->join[k], cudaEventDisableTiming));
+  }
+  p->nstream = n;
+  return FSTAT_OK;
+}
+
 int fstat_get_cta(const fstat_plan* p, int* ca, int* va, int* cb, int* vb) {
   if (!p || !ca || !va || !cb || !vb) return FSTAT_ERR_INVALID_ARG;
   *ca = p->ca;
@@ -645,8 +668,8 @@ std::string tune_key(const fstat_plan* p) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) prop.name[0] = 0;
   char buf[400];
-  std::snprintf(buf, sizeof buf, "%s|N=%lld|nfft=%lld|prec=%d|ndet=%d", prop.name,
-                (long long)p->d.n_samples, (long long)p->d.n_fft, p->d.precision, p->d.n_det);
+  std::snprintf(buf, sizeof buf, "%s|N=%lld|nfft=%lld|prec=%d|ndet=%d|ns=%d", prop.name,
+                (long long)p->d.n_samples, (long long)p->d.n_fft, p->d.precision, p->d.n_det, p->nstream);
   for (char* c = buf; *c; ++c)
     if (*c == ' ' || *c == '\t') *c = '_';
   return buf;
@@ -715,13 +738,19 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
       return FSTAT_OK;
     }
   }
-  int rc = ensure_capacity(p, 1);
+  const int kPipe = 8;  // templates in the overlapped pipeline timing
+  int rc = ensure_capacity(p, kPipe);
   if (rc) return rc;
   if (p->staged_pending) { CK(cudaEventSynchronize(p->staged)); p->staged_pending = false; }
-  p->h_tmpl[0] = fstat_template{0.3, -0.5, -1e-10, 0.0};
-  p->h_order[0] = 0;
-  CK(cudaMemcpyAsync(p->d_tmpl, p->h_tmpl, sizeof(fstat_template), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(p->d_order, p->h_order, sizeof(int), cudaMemcpyHostToDevice, st));
+  for (int k = 0; k < kPipe; ++k) {
+    p->h_tmpl[k] = fstat_template{0.3, -0.5, -1e-10 * (k + 1), 0.0};
+    p->h_order[k] = k;
+  }
+  CK(cudaMemcpyAsync(p->d_tmpl, p->h_tmpl, kPipe * sizeof(fstat_template), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(p->d_order, p->h_order, kPipe * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<fstat_template> ht(p->h_tmpl, p->h_tmpl + kPipe);
+  std::vector<int> ho(p->h_order, p->h_order + kPipe);
   float* out = nullptr;
   CK(cudaMalloc(&out, (size_t)p->d.n_fft * sizeof(float)));
   cudaEvent_t e0, e1;
@@ -732,26 +761,53 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
   float best_ms = 1e30f;
   static const int kCa[] = {0, 1, 2, 4};
   static const int kCb[] = {0, 1, 2, 4, 8};
+  const bool saved_prof = p->prof;
+  p->prof = false;
   for (int l1 = lo; l1 <= hi && rc == FSTAT_OK; ++l1) {
     rc = set_split(p, l1);
     if (rc) break;
     rc = run_sky(p, 0.3, -0.5, st);
     if (rc) break;
-    launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, 0, 1, p->d_coef, st);
-    float ba = 1e30f, bb = 1e30f;
-    int ca = 0, cb = 0, va = 0, vb = 0;
+    launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, 0, kPipe, p->d_coef, st);
+    // isolated timings of every compiled shape of each pass
+    std::vector<std::pair<float, std::pair<int, int>>> ta, tb;
     for (int v = 0; v < 2; ++v) {
       for (int c : kCa) {
         float ms = time_pass(p, 0, c, v, p->d_coef, out, st, e0, e1);
-        if (ms > 0.f && ms < ba) { ba = ms; ca = c; va = v; }
+        if (ms > 0.f) ta.push_back({ms, {c, v}});
       }
       for (int c : kCb) {
         float ms = time_pass(p, 1, c, v, p->d_coef, out, st, e0, e1);
-        if (ms > 0.f && ms < bb) { bb = ms; cb = c; vb = v; }
+        if (ms > 0.f) tb.push_back({ms, {c, v}});
       }
     }
-    if (ba + bb < best_ms) { best_ms = ba + bb; best = Choice{l1, ca, va, cb, vb}; }
+    std::sort(ta.begin(), ta.end());
+    std::sort(tb.begin(), tb.end());
+    // the best few of each, paired in the overlapped template pipeline
+    for (size_t ia = 0; ia < std::min<size_t>(3, ta.size()); ++ia) {
+      for (size_t ib = 0; ib < std::min<size_t>(3, tb.size()); ++ib) {
+        p->ca = ta[ia].second.first;
+        p->va = ta[ia].second.second;
+        p->cb = tb[ib].second.first;
+        p->vb = tb[ib].second.second;
+        int r = enqueue_compute(p, ht.data(), ho.data(), kPipe, p->d_tmpl, p->d_order, p->d_coef, out, 1, st,
+                                false, false);
+        if (r) { cudaGetLastError(); continue; }
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2; ++rep)
+          enqueue_compute(p, ht.data(), ho.data(), kPipe, p->d_tmpl, p->d_order, p->d_coef, out, 1, st, false,
+                          false);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = FSTAT_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 2 * kPipe;
+        if (ms < best_ms) { best_ms = ms; best = Choice{l1, p->ca, p->va, p->cb, p->vb}; }
+      }
+      if (rc) break;
+    }
   }
+  p->prof = saved_prof;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(out);

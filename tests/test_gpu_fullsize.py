@@ -112,3 +112,48 @@ def test_full_size_ten_day_two_detector_workload():
         v = got[i, inj.bin_index]
         sd = np.sqrt(2.0 * (4.0 + 2.0 * inj.rho2))
         assert abs(v - (4.0 + inj.rho2)) < 5.0 * sd + 0.02 * inj.rho2, (inj.rho2, v)
+
+
+def test_full_size_120_day_search_slice():
+    # 120 days at dt = 1 s (10 368 000 samples per detector), FFT 2^24, the
+    # sky patch of the large search: two sky positions with their injections,
+    # 2F at injected and random bins against the oracle's direct DFT sums.
+    from workloads import config5
+
+    t = config5()
+    skies = []
+    for inj in t.injections:
+        if (inj.alpha, inj.delta) not in skies:
+            skies.append((inj.alpha, inj.delta))
+        if len(skies) == 2:
+            break
+    injs = [i for i in t.injections if (i.alpha, i.delta) in skies][:3]
+    x = synth.make_data(t, injections=injs)
+    rng = np.random.default_rng(5)
+    rows = np.empty(len(injs) + 1, dtype=pkg.TEMPLATE_DTYPE)
+    for k, inj in enumerate(injs):
+        rows[k] = (inj.alpha, inj.delta, inj.f1dot, inj.f2dot)
+    rows[-1] = (skies[0][0], skies[0][1], t.f1dots[100], t.f2dots[3])
+    with pkg.FstatPlan.from_target(t) as plan:
+        for X in range(2):
+            plan.set_data(X, x[X], t.sigmas[X])
+        plan.autotune()
+        got = plan.compute(rows).cpu().numpy()
+        plan.sync()
+    half, lim = t.n_fft // 2, int(0.4 * t.n_fft)
+    preps = {}
+    for k in range(len(rows)):
+        key = (float(rows["alpha"][k]), float(rows["delta"][k]))
+        if key not in preps:
+            preps[key] = resamp.sky_prep(t, x, *key)
+        bins = list(rng.integers(half - lim, half + lim, 12)) + list(rng.integers(0, t.n_fft, 4))
+        if k < len(injs):
+            m = injs[k].bin_index
+            bins += [m - 1, m, m + 1]
+        bins = np.array(bins)
+        ref = resamp.twoF_at_bins(t, preps[key], float(rows["f1dot"][k]), float(rows["f2dot"][k]), bins)
+        assert _ok(got[k, bins], ref), (k, np.max(np.abs(got[k, bins] - ref)))
+    for k, inj in enumerate(injs):
+        v = got[k, inj.bin_index]
+        sd = np.sqrt(2.0 * (4.0 + 2.0 * inj.rho2))
+        assert abs(v - (4.0 + inj.rho2)) < 5.0 * sd + 0.02 * inj.rho2, (inj.rho2, v)
