@@ -16,10 +16,12 @@ continuous gravitational wave searches", arXiv:2201.00451):
 * ``metrics``   -- the comparison metrics r1, r2, theta of Sec. 4.2.
 * ``grad``      -- 2F and its gradient in (f, f1dot, alpha, delta) at
                    arbitrary parameters, from the demodulation sums.
+* ``peaks``     -- threshold crossings and per-band maxima of 2F (Sec. 5.4,
+                   Sec. 4.1).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA
 library and never imports it.
 """
 
-from . import geometry, resamp, demod, synth, metrics, grad  # noqa: F401
+from . import geometry, resamp, demod, synth, metrics, grad, peaks  # noqa: F401
