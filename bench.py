@@ -135,16 +135,19 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
+def ncu_traffic(kernel: str, length: int, c: int, v: int):
+    """DRAM bytes per launch of one pass shape (FFT length, columns or rows
+    per CTA, radix schedule) from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        e = t[kernel]
-        if e.get("source_hash") == kernel_source_hash():
-            return float(e["dram_bytes_per_launch"])
-    except (OSError, KeyError, ValueError):
+        if t.get("source_hash") != kernel_source_hash():
+            return None
+        for e in t["entries"]:
+            if (e["kernel"], e["L"], e["c"], e["v"]) == (kernel, length, c, v):
+                return float(e["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError, TypeError):
         pass
     return None
 
@@ -310,8 +313,11 @@ def run_ours(args, rank, world, local_rank):
     avg_s = tot / 1e3 / max(nl, 1)
     name, bytes_alg = kinfo[dom]
     achieved = bytes_alg / avg_s / 1e9
+    ca, va, cb, vb = plan.cta
+    shape = (n2, ca, va) if dom == 0 else (n1, cb, vb)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": ncu_traffic(name), "kernel": name,
+            "frac": achieved / peak, "traffic": ncu_traffic(name, *shape), "kernel": name,
+            "kernel_shape": {"L": shape[0], "c": shape[1], "v": shape[2]},
             "peak_source": peak_kind,
             "kernels_ms_per_launch": {kinfo[k][0]: stats[k][1] / max(stats[k][0], 1) for k in (0, 1)},
             "per_sky_ms": stats[2][1] / max(stats[2][0], 1),
@@ -319,6 +325,19 @@ def run_ours(args, rank, world, local_rank):
                      "achieved_GBps": (16.0 * t.n_samples + 4.0 * n_fft) * value / world / 1e9,
                      "frac": (16.0 * t.n_samples + 4.0 * n_fft) * value / world / 1e9 / peak},
             "split": [n1, n2], "cta": list(plan.cta)}
+    # the FFT's arithmetic against the FP32 CUDA-core peak (5 N log2 N flops
+    # per complex transform, two transforms per template; the FP32 peak is
+    # SMs x 128 lanes x 2 flops x SM clock)
+    props = torch.cuda.get_device_properties(dev)
+    f32_peak = props.multi_processor_count * 128 * 2 * FP32_CLOCK_MHZ * 1e6 / 1e12
+    flops_t = 2 * 5 * n_fft * math.log2(n_fft)
+    flops_k = {0: 2 * 5 * n_fft * math.log2(n2), 1: 2 * 5 * n_fft * math.log2(n1)}
+    roof["alu"] = {"unit": "TFLOP/s", "peak": f32_peak, "peak_source": "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                   "flops_per_template": flops_t,
+                   "path_achieved": flops_t * value / world / 1e12,
+                   "path_frac": flops_t * value / world / 1e12 / f32_peak,
+                   "kernel_achieved": flops_k[dom] / avg_s / 1e12,
+                   "kernel_frac": flops_k[dom] / avg_s / 1e12 / f32_peak}
     plan.close()
 
     line = None
@@ -358,6 +377,9 @@ def run_ours(args, rank, world, local_rank):
     # end-to-end: host x_h (pinned) -> device, compute, 2F back to pinned host
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(t, xs, tm, chunk, dev, stream, args)
+        # the same job with the reduction on the device: only band maxima and
+        # threshold crossings come back
+        line["e2e_peaks"] = e2e_peaks(t, xs, tm, chunk, dev, stream, args)
 
     if rank == 0 and not args.no_cpu:
         cb, _, _ = cpu_oracle_timing(t, [x.astype(np.complex128) for x in xs], len(tm_all))
@@ -590,6 +612,92 @@ def e2e(t, xs, tm, chunk, dev, stream, args):
     return {"value": n / el, "unit": UNIT,
             "h2d_bytes_per_step": int(sum(x.nbytes for x in xs)),
             "d2h_bytes_per_step": int(len(tm) * n_fft * 4)}
+
+
+FP32_CLOCK_MHZ = 2070.0  # maximum SM clock of the GB300 (nvidia-smi clocks.max.sm)
+PEAK_BANDS = 256         # band maxima per template (W = 16384 bins = 7.8 mHz at FFT 2^22, dt 0.5 s)
+PEAK_THRESHOLD = 70.0    # the retention threshold of Sec. 5.4
+PEAK_CAPACITY = 1 << 16
+
+
+def e2e_peaks(t, xs, tm, chunk, dev, stream, args):
+    """End to end through fstat_compute_peaks: per step the pinned x_h go up,
+    every template's 2F is reduced on the device to 256 band maxima (value
+    and bin) plus the list of 2F > 70, and those come back to pinned host
+    buffers.  Also the device-only rate of the peaks mode (no copies)."""
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+
+    hx = [torch.from_numpy(x).pin_memory() for x in xs]
+    plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
+    for X in range(len(t.detectors)):
+        plan.set_data(X, hx[X].numpy(), t.sigmas[X])
+    plan.autotune(stream)
+    chunks = [(i, tm[i:i + chunk]) for i in range(0, len(tm), chunk)]
+    outs = [{"count": torch.zeros(1, dtype=torch.int64, device=dev),
+             "peaks": torch.empty((PEAK_CAPACITY, 4), dtype=torch.int32, device=dev)} for _ in range(2)]
+    hmax = torch.empty((len(tm), PEAK_BANDS), dtype=torch.float32, pin_memory=True)
+    hbin = torch.empty((len(tm), PEAK_BANDS), dtype=torch.int32, pin_memory=True)
+    hcount = torch.empty(2, dtype=torch.int64, pin_memory=True)
+    hpeaks = torch.empty((2, PEAK_CAPACITY, 4), dtype=torch.int32, pin_memory=True)
+    copy = torch.cuda.Stream(dev)
+    done = [torch.cuda.Event() for _ in range(2)]
+
+    def step(with_copies=True):
+        if with_copies:
+            for X in range(len(t.detectors)):
+                plan.set_data(X, hx[X].numpy(), t.sigmas[X])
+        for k in range(2):
+            outs[k]["count"].zero_()
+        for j, (i, c) in enumerate(chunks):
+            k = j & 1
+            stream.wait_event(done[k])
+            plan.compute_peaks(c, threshold=PEAK_THRESHOLD, n_bands=PEAK_BANDS, tmpl_offset=i,
+                               out=outs[k], stream=stream)
+            if with_copies:
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                copy.wait_event(ev)
+                with torch.cuda.stream(copy):
+                    hmax[i:i + len(c)].copy_(outs[k]["band_max"], non_blocking=True)
+                    hbin[i:i + len(c)].copy_(outs[k]["band_bin"], non_blocking=True)
+                done[k].record(copy)
+        if with_copies:
+            # the two crossing lists (each shared by every other chunk)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            copy.wait_event(ev)
+            with torch.cuda.stream(copy):
+                for k in range(2):
+                    hcount[k:k + 1].copy_(outs[k]["count"], non_blocking=True)
+                    hpeaks[k].copy_(outs[k]["peaks"], non_blocking=True)
+            copy.synchronize()
+        stream.synchronize()
+
+    step()
+    torch.cuda.synchronize(dev)
+    s = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - s
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(with_copies=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dev_s = e0.elapsed_time(e1) * 1e-3
+    n_cross = int(hcount.sum())
+    plan.close()
+    n = len(tm) * args.steps
+    return {"value": n / el, "unit": UNIT,
+            "h2d_bytes_per_step": int(sum(x.nbytes for x in xs)),
+            "d2h_bytes_per_step": int(hmax.nbytes + hbin.nbytes + hcount.nbytes + hpeaks.nbytes),
+            "output": f"{PEAK_BANDS} band maxima (2F, bin) per template + list of 2F > {PEAK_THRESHOLD:g}",
+            "crossings_per_step": n_cross,
+            "device_value": n / dev_s}
 
 
 def main():

@@ -128,6 +128,43 @@ int fstat_set_data(fstat_plan* plan, int det, const void* xh, int dtype, int64_t
 int fstat_compute(fstat_plan* plan, const fstat_template* tmpl, int64_t n_tmpl, float* twoF,
                   void* stream);
 
+/* Post-processing on the device (Sec. 5.4 keeps only 2F > 70 and does that
+ * selection on the GPU so the full band never reaches the host; Sec. 4.1
+ * names the per-band maximum as the simplest CPU-side reduction).  One bin
+ * of one template whose 2F crossed the threshold: */
+typedef struct {
+  int64_t tmpl;   /* tmpl_offset + index of the template in the call's array */
+  int32_t bin;    /* m, ascending frequency: f_m = f0 + m df (fstat_freq_axis) */
+  float twoF;
+} fstat_peak;     /* 16 bytes */
+
+typedef struct {
+  float threshold;             /* list every bin with 2F > threshold (NaN rejected) */
+  int32_t n_bands;             /* band maxima per template: 0 (none) or a power of two
+                                  <= n_fft; band b = bins [b W, (b+1) W), W = n_fft / n_bands */
+  int64_t tmpl_offset;         /* added to the call-local template index of each peak */
+  fstat_peak* peaks;           /* DEVICE [capacity]; may be NULL when capacity == 0 */
+  int64_t capacity;
+  unsigned long long* n_peaks; /* DEVICE counter (NULL: no list).  Every crossing adds 1,
+                                  also past capacity; the caller zeroes it, and calls may
+                                  append to one list */
+  float* band_max;             /* DEVICE [n_tmpl][n_bands] maximum 2F per band */
+  int32_t* band_bin;           /* DEVICE [n_tmpl][n_bands] its bin (smallest on ties); may be NULL */
+} fstat_peak_out;
+
+/* Steps (iii)-(vii) for n_tmpl templates like fstat_compute, but the last
+ * FFT pass reduces 2F on the device instead of writing every bin: it lists
+ * the crossings of `out->threshold` and keeps each band's maximum.  `tmpl`
+ * is a HOST array; every pointer in `out` is caller-owned DEVICE memory.
+ * The list holds min(*n_peaks, capacity) entries in no particular order;
+ * which crossings are kept once capacity is exceeded is unspecified.  The
+ * plan keeps an 8-byte key per band and template as scratch (grown on
+ * demand, which synchronises the device).  Errors: INVALID_ARG (neither a
+ * list nor bands requested, n_bands not a power of two or > n_fft, NULL
+ * buffers, NaN threshold), NOT_READY, OOM, CUDA. */
+int fstat_compute_peaks(fstat_plan* plan, const fstat_template* tmpl, int64_t n_tmpl,
+                        const fstat_peak_out* out, void* stream);
+
 /* 2F and its gradient at arbitrary (off-grid) parameters, for refinement.
  * For each candidate, eq. (Fstat) is evaluated with the demodulation
  * integrals of eqs. (Fa_DET)/(Fb_DET) (Sec. 2) summed directly over the

@@ -44,6 +44,7 @@ EXPORTS = (
     "fstat_strerror", "fstat_twoF_noalloc", "fstat_get_cta", "fstat_set_cta", "fstat_autotune",
     "fstat_grad", "fstat_batch_create", "fstat_batch_add", "fstat_batch_instantiate",
     "fstat_batch_launch", "fstat_batch_nodes", "fstat_batch_destroy", "fstat_set_streams",
+    "fstat_compute_peaks",
 )
 
 
@@ -80,6 +81,17 @@ class Template(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("delta", ctypes.c_double),
                 ("f1dot", ctypes.c_double), ("f2dot", ctypes.c_double)]
 
+
+class PeakOut(ctypes.Structure):
+    _fields_ = [
+        ("threshold", ctypes.c_float), ("n_bands", ctypes.c_int32), ("tmpl_offset", ctypes.c_int64),
+        ("peaks", ctypes.c_void_p), ("capacity", ctypes.c_int64), ("n_peaks", ctypes.c_void_p),
+        ("band_max", ctypes.c_void_p), ("band_bin", ctypes.c_void_p),
+    ]
+
+
+# fstat_peak: one threshold crossing (16 bytes)
+PEAK_DTYPE = np.dtype([("tmpl", "<i8"), ("bin", "<i4"), ("twoF", "<f4")])
 
 TEMPLATE_DTYPE = np.dtype([("alpha", "<f8"), ("delta", "<f8"), ("f1dot", "<f8"), ("f2dot", "<f8")])
 CANDIDATE_DTYPE = np.dtype([("f", "<f8"), ("f1dot", "<f8"), ("alpha", "<f8"), ("delta", "<f8"),
@@ -125,6 +137,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fstat_batch_nodes": (i32, [P, ctypes.POINTER(i64)]),
         "fstat_batch_destroy": (None, [P]),
         "fstat_set_streams": (i32, [P, i32]),
+        "fstat_compute_peaks": (i32, [P, P, i64, ctypes.POINTER(PeakOut), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -266,6 +279,41 @@ class FstatPlan:
                                      ctypes.c_void_p(out_ptr), _stream_handle(stream))
         _check(rc, "fstat_compute")
 
+    def compute_peaks(self, templates, threshold: float = 70.0, n_bands: int = 0, capacity: int = 4096,
+                      tmpl_offset: int = 0, out=None, stream=None):
+        """fstat_compute_peaks: 2F reduced on the device.  Returns a dict of
+        CUDA tensors: ``count`` (int64 [1], every crossing of ``threshold``),
+        ``peaks`` (int32 [capacity, 4]: template index lo/hi words, bin, 2F
+        bits; see :func:`peaks_to_numpy`), and for ``n_bands > 0``
+        ``band_max`` (float32 [n, n_bands]) and ``band_bin`` (int32).
+        ``out`` may pass such a dict back in to append to its list (its band
+        buffers are reused when their shape fits)."""
+        import torch
+        t = as_templates(templates)
+        n = len(t)
+        if out is None:
+            out = {"count": torch.zeros(1, dtype=torch.int64, device="cuda"),
+                   "peaks": torch.empty((max(capacity, 0), 4), dtype=torch.int32, device="cuda")}
+        if n_bands > 0:
+            for key, dt in (("band_max", torch.float32), ("band_bin", torch.int32)):
+                b = out.get(key)
+                if b is None or b.shape != (n, n_bands) or b.dtype != dt or not b.is_cuda:
+                    out[key] = torch.empty((n, n_bands), dtype=dt, device="cuda")
+        po = PeakOut()
+        po.threshold = float(threshold)
+        po.n_bands = int(n_bands)
+        po.tmpl_offset = int(tmpl_offset)
+        cap = out["peaks"].shape[0] if out.get("peaks") is not None else 0
+        po.peaks = out["peaks"].data_ptr() if cap else None
+        po.capacity = cap
+        po.n_peaks = out["count"].data_ptr() if out.get("count") is not None else None
+        po.band_max = out["band_max"].data_ptr() if n_bands > 0 else None
+        po.band_bin = out["band_bin"].data_ptr() if n_bands > 0 else None
+        rc = self._lib.fstat_compute_peaks(self._p, ctypes.c_void_p(t.ctypes.data), n, ctypes.byref(po),
+                                           _stream_handle(stream))
+        _check(rc, "fstat_compute_peaks")
+        return out
+
     def grad(self, candidates, stream=None):
         """fstat_grad: (2F [n], d2F/d(f, f1dot, alpha, delta) [n, 4]) as CUDA
         float32 tensors for a structured array of CANDIDATE_DTYPE."""
@@ -336,6 +384,12 @@ class FstatPlan:
     def autotune(self, stream=None):
         """fstat_autotune: pick the fastest FFT split and CTA shapes."""
         _check(self._lib.fstat_autotune(self._p, _stream_handle(stream)), "fstat_autotune")
+
+
+def peaks_to_numpy(out) -> np.ndarray:
+    """The filled part of a compute_peaks list as a PEAK_DTYPE array."""
+    n = min(int(out["count"].item()), out["peaks"].shape[0])
+    return out["peaks"][:n].cpu().numpy().copy().view(PEAK_DTYPE).reshape(n)
 
 
 class FstatBatch:

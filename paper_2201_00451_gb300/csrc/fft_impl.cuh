@@ -97,6 +97,17 @@ template <typename T, int L, int C, int V = 0> struct Buf {
   static constexpr size_t BYTES = NBUF * ONE;
 };
 
+// Peaks mode: a persistent pass-B CTA keeps the band keys of up to
+// kPeakBands bands in shared memory across its tiles and flushes them to
+// global memory once, when every band spans whole output rows (then each
+// band's bins in a tile sit in the same threads in every tile).
+constexpr int kPeakBands = 1024;
+template <typename T, int L, int C, int V> struct PeakSmem {
+  static constexpr size_t EXTRA = (size_t)kPeakBands * sizeof(unsigned long long);
+  static constexpr bool ACC = kPipeline && Buf<T, L, C, V>::BYTES + EXTRA <= 227 * 1024;
+  static constexpr size_t BYTES = Buf<T, L, C, V>::BYTES + (ACC ? EXTRA : 0);
+};
+
 template <typename T, int L, int C, int V = 0> constexpr bool cfg_ok() {
   using S = Shape<T, L, V>;
   return C * S::TPC >= 32 && C * S::TPC <= 1024 && Buf<T, L, C, V>::ONE <= kSmemCap;
@@ -421,11 +432,113 @@ k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int
 }
 
 // ------------------------------------------------------------- pass B
-template <typename T, int L, int CB, int V, bool STAGED>
+// Peaks epilogue.  sf holds the tile's 2F as [r][c] (r = ascending row of
+// the output, c = column of the CTA), so bin m = k2_0 + c + n2 r increases
+// with the flat index f = r CB + c.  Each thread takes E consecutive
+// values.  Band boundaries fall on multiples of a power of two in f (every
+// band is 2^log2_band consecutive bins and k2_0 is a multiple of CB), so
+// when no thread's run straddles one, the lanes of one band form an
+// aligned power-of-two group: a masked butterfly gives the group maximum
+// and the group's first lane alone updates the band key.
+template <int CB, int E>
+__device__ __forceinline__ void peak_epilogue(const float* sf, int k2_0, int n2, const PeakArgs& pk,
+                                              unsigned long long* ks) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int f0 = threadIdx.x * E;
+  float v[E];
+  if constexpr (E % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < E; j += 4) {
+      const float4 q = *reinterpret_cast<const float4*>(sf + f0 + j);
+      v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j] = sf[f0 + j];
+  }
+  auto bin = [&](int f) { return (unsigned)(k2_0 + (f & (CB - 1)) + n2 * (f / CB)); };
+  float best = v[0];
+  int jb = 0;
+#pragma unroll
+  for (int j = 1; j < E; ++j)
+    if (v[j] > best) { best = v[j]; jb = j; }
+  const int lane = threadIdx.x & 31;
+  if (pk.count && __any_sync(FULL, best > pk.thr)) {
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const bool hit = v[j] > pk.thr;
+      const unsigned bal = __ballot_sync(FULL, hit);
+      if (!bal) continue;
+      const int leader = __ffs(bal) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(pk.count, (unsigned long long)__popc(bal));
+      base = __shfl_sync(FULL, base, leader);
+      if (hit) {
+        const unsigned long long idx = base + __popc(bal & ((1u << lane) - 1u));
+        if (idx < (unsigned long long)pk.cap) {
+          fstat_peak e;
+          e.tmpl = pk.tmpl;
+          e.bin = (int32_t)bin(f0 + j);
+          e.twoF = v[j];
+          pk.peaks[idx] = e;
+        }
+      }
+    }
+  }
+  if (pk.band_key) {
+    // shared keys of this CTA when it accumulates, else the global row
+    unsigned long long* keys = ks ? ks : pk.band_key;
+    const int lb = pk.log2_band;
+    // a band is a run of 2^lp consecutive f: CB W / n2 when it spans whole
+    // rows, else the CTA's part of one row (at most CB values)
+    constexpr int LCB = log2c(CB), LE = log2c(E);
+    const int ln2 = 31 - __clz(n2);
+    const int lp = lb >= ln2 ? LCB + lb - ln2 : (lb < LCB ? lb : LCB);
+    // In shared keys, a band within one warp's values has a single writer
+    // (the same lane in every tile), so a plain update suffices.
+    const bool excl = ks != nullptr && lp <= LE + 5;
+    auto update = [&](unsigned b, unsigned long long key) {
+      if (excl) {
+        if (key > keys[b]) keys[b] = key;
+      } else {
+        atomicMax(keys + b, key);
+      }
+    };
+    if (lp >= LE) {
+      // the run lies in one band; lanes of a band form an aligned group
+      const unsigned band = bin(f0) >> lb;
+      unsigned long long key = band_key(best, bin(f0 + jb));
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long ok = __shfl_xor_sync(FULL, key, o);
+        if (o < (1 << (lp - LE)) && ok > key) key = ok;
+      }
+      if ((lane & ((1 << (lp - LE < 5 ? lp - LE : 5)) - 1)) == 0) update(band, key);
+    } else {
+      // runs of P values, each one band, inside this thread's values
+      const int pm = (1 << lp) - 1;
+      float bv = v[0];
+      int bj = 0;
+#pragma unroll
+      for (int j = 1; j < E; ++j) {
+        if ((j & pm) == 0) {
+          update(bin(f0 + bj) >> lb, band_key(bv, bin(f0 + bj)));
+          bv = v[j]; bj = j;
+        } else if (v[j] > bv) {
+          bv = v[j]; bj = j;
+        }
+      }
+      update(bin(f0 + bj) >> lb, band_key(bv, bin(f0 + bj)));
+    }
+  }
+}
+
+template <typename T, int L, int CB, int V, bool STAGED, bool PEAK>
 __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type* buf, int c, int t,
                                             const typename PairMem<T>::type* __restrict__ Z, int n2,
                                             const typename TwT<T>::type* __restrict__ twL, T kA, T kB, T kC,
-                                            float* __restrict__ out) {
+                                            float* __restrict__ out, const PeakArgs& pk,
+                                            unsigned long long* ks) {
   using S = Shape<T, L, V>;
   const int k2 = tile * CB + c;
   Pair<T> v[S::R0];
@@ -439,6 +552,8 @@ __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type*
   passes<T, L, V, CB, 1, kPassBTable && sizeof(T) == 4>(v, buf, t, twL);
 
   constexpr int NB = S::R0 / S::RL;
+  float* sf = reinterpret_cast<float*>(buf - c);  // the CTA's stage, reused by the peaks epilogue
+  if constexpr (PEAK) __syncthreads();            // every thread is done with the exchange buffer
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int b = t + q * S::TPC;
@@ -450,17 +565,25 @@ __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type*
       T fb2 = x.br * x.br + x.bi * x.bi;
       T re = x.ar * x.br + x.ai * x.bi;
       T tf = kB * fa2 + kA * fb2 - kC * re;
-      const int m = k2 + n2 * ((k1 + L / 2) & (L - 1));
-      __stcs(out + m, (float)tf);  // streaming store: keep G and Z in L2
+      const int r = (k1 + L / 2) & (L - 1);
+      if constexpr (PEAK) {
+        sf[r * CB + c] = (float)tf;
+      } else {
+        __stcs(out + k2 + n2 * r, (float)tf);  // streaming store: keep G and Z in L2
+      }
     }
+  }
+  if constexpr (PEAK) {
+    __syncthreads();
+    peak_epilogue<CB, L * CB / (CB * S::TPC)>(sf, tile * CB, n2, pk, ks);
   }
 }
 
-template <typename T, int L, int CB, int V>
+template <typename T, int L, int CB, int V, bool PEAK>
 __global__ void __launch_bounds__(CB * Shape<T, L, V>::TPC, (min_blocks<T, L, CB, V>()))
 k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
          const typename TwT<T>::type* __restrict__ twL, const SkyConst* __restrict__ sky,
-         float* __restrict__ out) {
+         float* __restrict__ out, const PeakArgs pk) {
   using S = Shape<T, L, V>;
   using B = Buf<T, L, CB, V>;
   using PM = typename PairMem<T>::type;
@@ -471,8 +594,21 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
   T kA, kB, kC;
   if constexpr (sizeof(T) == 4) { kA = sky->kAf; kB = sky->kBf; kC = sky->kCf; }
   else { kA = sky->kA; kB = sky->kB; kC = sky->kC; }
+  // peaks mode with whole-row bands: this CTA's band keys in shared memory
+  unsigned long long* ks = nullptr;
+  int n_bands = 0;
+  if constexpr (PEAK && PeakSmem<T, L, CB, V>::ACC) {
+    if (pk.band_key && pk.log2_band >= 31 - __clz(n2)) {
+      n_bands = (L * n2) >> pk.log2_band;
+      if (n_bands <= kPeakBands) {
+        ks = reinterpret_cast<unsigned long long*>(smem_raw + Buf<T, L, CB, V>::BYTES);
+        for (int b = threadIdx.x; b < n_bands; b += blockDim.x) ks[b] = 0ull;
+        // visible to the epilogue after the tile loop's first barrier
+      }
+    }
+  }
   if constexpr (!kPipeline) {
-    pass_b_tile<T, L, CB, V, false>(blockIdx.x, smem + c, c, t, Z, n2, twL, kA, kB, kC, out);
+    pass_b_tile<T, L, CB, V, false, PEAK>(blockIdx.x, smem + c, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks);
   } else {
     const int n_tiles = n2 / CB;
     auto stage = [&](int it) { return smem + (B::NBUF == 2 ? (it & 1) : 0) * (CB * S::LP) + c; };
@@ -501,8 +637,14 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
         cp_async_wait<0>();
       }
       __syncthreads();
-      pass_b_tile<T, L, CB, V, true>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out);
+      pass_b_tile<T, L, CB, V, true, PEAK>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks);
       __syncthreads();  // this buffer is the prefetch target two tiles on
+    }
+    if constexpr (PEAK) {
+      if (ks) {  // the loop ended on a barrier: every tile's keys are in
+        for (int b = threadIdx.x; b < n_bands; b += blockDim.x)
+          if (ks[b]) atomicMax(pk.band_key + b, ks[b]);
+      }
     }
   }
 }
@@ -544,21 +686,24 @@ cudaError_t run_a(const void* G, int64_t lc, int64_t n, int n1, const void* twA,
   return cudaGetLastError();
 }
 
-template <typename T, int L, int CB, int V>
-cudaError_t run_b(const void* Z, int n2, const void* twB, const SkyConst* sky, float* out, cudaStream_t st) {
+template <typename T, int L, int CB, int V, bool PEAK>
+cudaError_t run_b(const void* Z, int n2, const void* twB, const SkyConst* sky, float* out, const PeakArgs& pk,
+                  cudaStream_t st) {
   using S = Shape<T, L, V>;
-  constexpr size_t smem = Buf<T, L, CB, V>::BYTES;
+  constexpr size_t smem = PEAK ? PeakSmem<T, L, CB, V>::BYTES : Buf<T, L, CB, V>::BYTES;
   constexpr int threads = CB * S::TPC;
+  static_assert(!PEAK || (L * CB * sizeof(float) <= Buf<T, L, CB, V>::ONE), "peaks epilogue reuses the stage");
+  static_assert(!PEAK || threads % 32 == 0, "peaks epilogue works on whole warps");
   static int ctas = 0;
   if (!ctas) {
-    cudaError_t e = resident_ctas(k_pass_b<T, L, CB, V>, threads, smem, &ctas);
+    cudaError_t e = resident_ctas(k_pass_b<T, L, CB, V, PEAK>, threads, smem, &ctas);
     if (e != cudaSuccess) return e;
   }
   if (n2 % CB) return cudaErrorInvalidConfiguration;
   const int tiles = n2 / CB;
   const int grid = (!kPipeline || tiles < ctas) ? tiles : ctas;
-  k_pass_b<T, L, CB, V><<<grid, threads, smem, st>>>(
-      (const typename S::PM*)Z, n2, (const typename S::TW*)twB, sky, out);
+  k_pass_b<T, L, CB, V, PEAK><<<grid, threads, smem, st>>>(
+      (const typename S::PM*)Z, n2, (const typename S::TW*)twB, sky, out, pk);
   return cudaGetLastError();
 }
 
@@ -594,57 +739,57 @@ cudaError_t pick_a(int ca, int v, const void* G, int64_t lc, int64_t n, int n1, 
   return cudaErrorInvalidConfiguration;
 }
 
-template <typename T, int L, int V>
+template <typename T, int L, int V, bool PEAK>
 cudaError_t pick_b_v(int cb, const void* Z, int n2, const void* twB, const SkyConst* sky, float* out,
-                     cudaStream_t st) {
+                     const PeakArgs& pk, cudaStream_t st) {
   switch (cb) {
-    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_b<T, L, 1, V>(Z, n2, twB, sky, out, st); break;
-    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_b<T, L, 2, V>(Z, n2, twB, sky, out, st); break;
-    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_b<T, L, 4, V>(Z, n2, twB, sky, out, st); break;
-    case 8: if constexpr (cfg_ok<T, L, 8, V>()) return run_b<T, L, 8, V>(Z, n2, twB, sky, out, st); break;
+    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_b<T, L, 1, V, PEAK>(Z, n2, twB, sky, out, pk, st); break;
+    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_b<T, L, 2, V, PEAK>(Z, n2, twB, sky, out, pk, st); break;
+    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_b<T, L, 4, V, PEAK>(Z, n2, twB, sky, out, pk, st); break;
+    case 8: if constexpr (cfg_ok<T, L, 8, V>()) return run_b<T, L, 8, V, PEAK>(Z, n2, twB, sky, out, pk, st); break;
     default: break;
   }
   return cudaErrorInvalidConfiguration;
 }
 
-template <typename T, int L>
+template <typename T, int L, bool PEAK>
 cudaError_t pick_b(int cb, int v, const void* Z, int n2, const void* twB, const SkyConst* sky, float* out,
-                   cudaStream_t st) {
+                   const PeakArgs& pk, cudaStream_t st) {
   using S = Shape<T, L, 0>;
   if (cb <= 0) cb = S::CB_DEF;
-  if (v == 0 && cb == S::CB_DEF) return run_b<T, L, S::CB_DEF, 0>(Z, n2, twB, sky, out, st);
+  if (v == 0 && cb == S::CB_DEF) return run_b<T, L, S::CB_DEF, 0, PEAK>(Z, n2, twB, sky, out, pk, st);
   if constexpr (sizeof(T) == 4 && wide_variants<L>()) {
-    if (v == 0) return pick_b_v<T, L, 0>(cb, Z, n2, twB, sky, out, st);
+    if (v == 0) return pick_b_v<T, L, 0, PEAK>(cb, Z, n2, twB, sky, out, pk, st);
     if constexpr (L >= 1024)
-      if (v == 1) return pick_b_v<T, L, 1>(cb, Z, n2, twB, sky, out, st);
+      if (v == 1) return pick_b_v<T, L, 1, PEAK>(cb, Z, n2, twB, sky, out, pk, st);
   }
   return cudaErrorInvalidConfiguration;
 }
 
 #define FSTAT_LEN_CASES(F, ...)            \
-  case 5: return F<T, 32>(__VA_ARGS__);    \
-  case 6: return F<T, 64>(__VA_ARGS__);    \
-  case 7: return F<T, 128>(__VA_ARGS__);   \
-  case 8: return F<T, 256>(__VA_ARGS__);   \
-  case 9: return F<T, 512>(__VA_ARGS__);   \
-  case 10: return F<T, 1024>(__VA_ARGS__); \
-  case 11: return F<T, 2048>(__VA_ARGS__); \
-  case 12: return F<T, 4096>(__VA_ARGS__);
+  case 5: return F<T, 32 __VA_ARGS__;    \
+  case 6: return F<T, 64 __VA_ARGS__;    \
+  case 7: return F<T, 128 __VA_ARGS__;   \
+  case 8: return F<T, 256 __VA_ARGS__;   \
+  case 9: return F<T, 512 __VA_ARGS__;   \
+  case 10: return F<T, 1024 __VA_ARGS__; \
+  case 11: return F<T, 2048 __VA_ARGS__; \
+  case 12: return F<T, 4096 __VA_ARGS__;
 
 template <typename T>
 cudaError_t dispatch_a(int log2_n2, int ca, int v, const void* G, int64_t lc, int64_t n, int n1, const void* twA,
                        const void* hi, const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st) {
   switch (log2_n2) {
-    FSTAT_LEN_CASES(pick_a, ca, v, G, lc, n, n1, twA, hi, lo, h, coef, Z, st)
+    FSTAT_LEN_CASES(pick_a, >(ca, v, G, lc, n, n1, twA, hi, lo, h, coef, Z, st))
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename T>
+template <typename T, bool PEAK>
 cudaError_t dispatch_b(int log2_n1, int cb, int v, const void* Z, int n2, const void* twB, const SkyConst* sky,
-                       float* out, cudaStream_t st) {
+                       float* out, const PeakArgs& pk, cudaStream_t st) {
   switch (log2_n1) {
-    FSTAT_LEN_CASES(pick_b, cb, v, Z, n2, twB, sky, out, st)
+    FSTAT_LEN_CASES(pick_b, , PEAK>(cb, v, Z, n2, twB, sky, out, pk, st))
     default: return cudaErrorInvalidValue;
   }
 }

@@ -126,17 +126,48 @@ struct TwiddleTables {
 TwiddleTables twiddle_layout(int precision, int log2n1, int log2n2, void* base);
 cudaError_t build_twiddles(int precision, int log2n1, int log2n2, void* base, cudaStream_t st);
 
+// Peaks mode of pass B: the 2F of one template is reduced in the kernel
+// instead of being written bin by bin (fstat_compute_peaks).
+struct PeakArgs {
+  unsigned long long* band_key;  // this template's row of band keys, or nullptr
+  fstat_peak* peaks;             // crossing list [cap]
+  unsigned long long* count;     // list counter, or nullptr (no list)
+  long long cap;
+  long long tmpl;                // template index stored with each crossing
+  float thr;
+  int log2_band;                 // log2(bins per band)
+};
+
+// Band key: order-preserving image of the float 2F in the high word, the
+// complement of the bin in the low word, so an unsigned maximum picks the
+// largest 2F and, among equal values, the smallest bin.  0 = no value.
+__device__ __forceinline__ unsigned long long band_key(float v, unsigned bin) {
+  unsigned u = __float_as_uint(v);
+  u ^= (u & 0x80000000u) ? 0xffffffffu : 0x80000000u;
+  return ((unsigned long long)u << 32) | (unsigned long long)(0xffffffffu - bin);
+}
+
 // FFT passes; ca / cb = columns / rows per CTA (0 = default for the length),
 // va / vb = radix schedule (0 = radix-16 first, 1 = radix-8 first).
 cudaError_t launch_pass_a_f32(int log2_n2, int ca, int va, const void* G, int64_t lc, int64_t n, int n1,
                               const void* twA, const void* hi, const void* lo, int h, const TmplCoef* coef,
                               void* Z, cudaStream_t st);
+// pk == nullptr: write 2F to out[n_fft]; otherwise reduce it as pk says.
 cudaError_t launch_pass_b_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
-                              const SkyConst* sky, float* out, cudaStream_t st);
+                              const SkyConst* sky, float* out, cudaStream_t st,
+                              const PeakArgs* pk = nullptr);
 cudaError_t launch_pass_a_f64(int log2_n2, int ca, int va, const void* G, int64_t lc, int64_t n, int n1,
                               const void* twA, const void* hi, const void* lo, int h, const TmplCoef* coef,
                               void* Z, cudaStream_t st);
 cudaError_t launch_pass_b_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
-                              const SkyConst* sky, float* out, cudaStream_t st);
+                              const SkyConst* sky, float* out, cudaStream_t st,
+                              const PeakArgs* pk = nullptr);
+cudaError_t launch_pass_b_peak_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
+                                   const SkyConst* sky, const PeakArgs& pk, cudaStream_t st);
+cudaError_t launch_pass_b_peak_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
+                                   const SkyConst* sky, const PeakArgs& pk, cudaStream_t st);
+// Band keys of n rows x n_bands -> maximum 2F and its bin (band_bin may be null).
+cudaError_t launch_band_decode(const unsigned long long* keys, int64_t count, float* band_max,
+                               int32_t* band_bin, cudaStream_t st);
 
 }  // namespace fstat
