@@ -79,18 +79,38 @@ def step_iv(target, t_b, det, alpha, delta, iters: int = 3):
     return T
 
 
-def dirichlet_weight(x, n: int, dterms: int):
-    """Truncated, Hamming-tapered Dirichlet kernel W(x) (W(0) = 1)."""
+TAPERED, UNTAPERED, PERIODIC = 0, 1, 2
+
+
+def dirichlet_weight(x, n: int, dterms: int, kind: int = TAPERED):
+    """Interpolation weight W(x), W(0) = 1, for the kernels the step-(v)
+    interpolator can use (the paper names none; see the readings):
+
+    TAPERED    sin(pi x) / (n sin(pi x / n)) * (0.54 + 0.46 cos(pi x / (D + 1)))
+               (Dirichlet kernel of the full n-sample series, truncated to
+               2D + 1 taps, Hamming taper)
+    UNTAPERED  sin(pi x) / (n sin(pi x / n))            (truncated, no taper)
+    PERIODIC   sin(pi x) / (M sin(pi x / M)), M = 2D + 1 (Dirichlet kernel of
+               the 2D + 1 taps themselves)
+    """
     x = np.asarray(x, dtype=np.float64)
     out = np.ones_like(x)
     nz = x != 0.0
     xs = x[nz]
-    out[nz] = (np.sin(np.pi * xs) / (n * np.sin(np.pi * xs / n))
-               * (0.54 + 0.46 * np.cos(np.pi * xs / (dterms + 1))))
+    if kind == PERIODIC:
+        m = 2 * dterms + 1
+        out[nz] = np.sin(np.pi * xs) / (m * np.sin(np.pi * xs / m))
+    elif kind == UNTAPERED:
+        out[nz] = np.sin(np.pi * xs) / (n * np.sin(np.pi * xs / n))
+    elif kind == TAPERED:
+        out[nz] = (np.sin(np.pi * xs) / (n * np.sin(np.pi * xs / n))
+                   * (0.54 + 0.46 * np.cos(np.pi * xs / (dterms + 1))))
+    else:
+        raise ValueError(f"unknown interpolation kernel {kind}")
     return out
 
 
-def step_v(z, u, dterms: int):
+def step_v(z, u, dterms: int, kind: int = TAPERED):
     """Interpolate z at fractional sample positions u (units of dt from t_0).
 
     Returns (values, valid).  k0 = rint(u); taps k0-D..k0+D; out-of-range
@@ -103,7 +123,7 @@ def step_v(z, u, dterms: int):
     for m in range(-dterms, dterms + 1):
         k = k0 + m
         ok = valid & (k >= 0) & (k < n)
-        w = dirichlet_weight(dlt - m, n, dterms)
+        w = dirichlet_weight(dlt - m, n, dterms, kind)
         out[ok] += z[k[ok]] * w[ok]
     exact = valid & (dlt == 0.0)
     out[exact] = z[k0[exact]]
@@ -124,7 +144,7 @@ def sky_prep(target, xh_list, alpha: float, delta: float) -> dict:
         z = step_iii(target, xh_list[X], det, alpha, delta)
         T = step_iv(target, t_b, det, alpha, delta)
         u = (T - target.t0) / target.dt
-        zi, valid = step_v(z, u, target.dterms)
+        zi, valid = step_v(z, u, target.dterms, getattr(target, "interp", TAPERED))
         a, b = geo.antenna_ab(T, det, alpha, delta, target.ephemeris)
         a = np.where(valid, a, 0.0)
         b = np.where(valid, b, 0.0)

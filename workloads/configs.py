@@ -104,6 +104,7 @@ class Target:
     seed: int = 0
     t_ref: float = float("nan")      # NaN -> t0 + (n_samples // 2) * dt
     ephemeris: dict = field(default_factory=lambda: dict(EPHEMERIS))
+    interp: int = 0                  # interpolation kernel: 0 tapered Dirichlet, 1 untapered, 2 periodic 2D+1
 
     @property
     def t_span(self) -> float:
@@ -256,7 +257,7 @@ def config5(realisation: int = 0) -> Target:
 def small_target(n_samples=3001, dt=2.0, n_fft=1 << 13, n_det=1, f_het=100.0,
                  skies=None, f1dots=(0.0,), f2dots=(0.0,), seed=7, dtype="c128",
                  sigmas=None, t0=0.0, dterms=8, n_inj=0, rho2_range=(100.0, 100.0),
-                 t_ref=float("nan"), detectors=None) -> Target:
+                 t_ref=float("nan"), detectors=None, interp=0) -> Target:
     """A small data set for tests: sizes chosen by the caller, defaults give a
     ragged sample count (not a multiple of any tile) padded to 2^13."""
     if detectors is None:
@@ -270,7 +271,7 @@ def small_target(n_samples=3001, dt=2.0, n_fft=1 << 13, n_det=1, f_het=100.0,
         name="small", detectors=tuple(detectors), t0=t0, dt=dt, n_samples=n_samples,
         f_het=f_het, n_fft=n_fft, dterms=dterms, sigmas=tuple(sigmas), dtype=dtype,
         skies=tuple(skies), f1dots=np.asarray(f1dots, dtype=np.float64),
-        f2dots=np.asarray(f2dots, dtype=np.float64), seed=seed, t_ref=t_ref,
+        f2dots=np.asarray(f2dots, dtype=np.float64), seed=seed, t_ref=t_ref, interp=interp,
     )
     if n_inj:
         t.injections = draw_injections(t, n_inj=n_inj, rho2_range=rho2_range,
