@@ -18,10 +18,13 @@ continuous gravitational wave searches", arXiv:2201.00451):
                    arbitrary parameters, from the demodulation sums.
 * ``peaks``     -- threshold crossings and per-band maxima of 2F (Sec. 5.4,
                    Sec. 4.1).
+* ``semicoh``   -- semi-coherent sum of per-segment 2F with nearest-bin
+                   sliding (Sec. 6).
+* ``interp_study`` -- accuracy of the step-(v) interpolator variants.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA
 library and never imports it.
 """
 
-from . import geometry, resamp, demod, synth, metrics, grad, peaks  # noqa: F401
+from . import geometry, resamp, demod, synth, metrics, grad, peaks, semicoh  # noqa: F401

@@ -21,6 +21,8 @@ from .configs import (  # noqa: F401
     config2,
     config3,
     config5,
+    segment_slices,
     small_target,
+    split_segments,
 )
 from .gen import make_noise, template_grid  # noqa: F401

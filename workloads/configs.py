@@ -10,6 +10,7 @@ seeded Gaussian noise plus injected signals stand in for them.
 
 from __future__ import annotations
 
+import dataclasses
 import math
 from dataclasses import dataclass, field
 
@@ -278,3 +279,27 @@ def small_target(n_samples=3001, dt=2.0, n_fft=1 << 13, n_det=1, f_het=100.0,
                                        min_sep_bins=min(200, n_fft // (4 * n_inj)),
                                        seed=seed)
     return t
+
+
+def split_segments(t: Target, n_seg: int) -> list:
+    """Equal consecutive segments of a target's sample grid (the last one
+    takes any remainder) for a semi-coherent search: each keeps the target's
+    detectors, dt, f_h, n_fft, noise levels, sky and spindown grids, and
+    gets its own reference time (its midpoint).  Slice the data with
+    ``segment_slices``."""
+    n = t.n_samples // n_seg
+    out = []
+    for k in range(n_seg):
+        start = k * n
+        cnt = n if k < n_seg - 1 else t.n_samples - start
+        out.append(dataclasses.replace(
+            t, name=f"{t.name}.seg{k}", t0=t.t0 + start * t.dt, n_samples=cnt, injections=(),
+            t_ref=float("nan")))
+    return out
+
+
+def segment_slices(t: Target, n_seg: int) -> list:
+    """(start, count) of each segment of ``split_segments``."""
+    n = t.n_samples // n_seg
+    return [(k * n, n if k < n_seg - 1 else t.n_samples - k * n) for k in range(n_seg)]
+
