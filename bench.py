@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-interp", action="store_true")
     ap.add_argument("--streams", type=int, default=2, help="template streams per plan (1..4)")
     ap.add_argument("--shape", default="", help="n1,ca,va,cb,vb: fixed FFT split and CTA shapes (skip autotune)")
     return ap.parse_args()
@@ -366,6 +367,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_large:
         line["large_search"] = large_bench(dev, stream)
 
+    # per-sky cost of the step-(v) interpolator variants and half-widths
+    if rank == 0 and not args.no_interp:
+        line["interp_cost"] = interp_cost(t, xs, tm_all, dev, stream)
+
     # FP64-GPU comparison path (same kernels in FP64), timed on a subset
     if rank == 0 and not args.no_fp64:
         line["fp64_gpu"] = fp64_gpu(t, xs, tm_all, args.fp64_templates, dev, stream, value)
@@ -386,6 +391,37 @@ def run_ours(args, rank, world, local_rank):
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def interp_cost(t, xs, tm_all, dev, stream, reps=5):
+    """Per-sky work (steps iii-v, 2 x 1 728 000 samples) in ms for each
+    interpolation kernel and half-width D (the FFT passes do not depend on
+    them)."""
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+
+    names = {pkg.INTERP_TAPERED: "tapered", pkg.INTERP_UNTAPERED: "untapered",
+             pkg.INTERP_PERIODIC: "periodic"}
+    out = torch.empty((1, t.n_fft), dtype=torch.float32, device=dev)
+    res = {}
+    for kind, name in names.items():
+        row = {}
+        for d in (4, 8, 16, 32):
+            plan = pkg.FstatPlan.from_target(t, pkg.MIXED, dterms=d, interp=kind)
+            for X in range(len(t.detectors)):
+                plan.set_data(X, xs[X], t.sigmas[X])
+            plan.compute_ptr(tm_all[:1], out.data_ptr(), stream)
+            plan.set_profiling(True)
+            for _ in range(reps):
+                plan.invalidate_sky()
+                plan.compute_ptr(tm_all[:1], out.data_ptr(), stream)
+            n, tot = plan.kernel_stats(2)
+            plan.set_profiling(False)
+            plan.close()
+            row[f"D{d}"] = tot / max(n, 1)
+        res[name] = row
+    return {"unit": "ms per sky position", "per_sky_ms": res}
 
 
 def fp64_gpu(t, xs, tm_all, n, dev, stream, mixed_value):

@@ -53,6 +53,13 @@ enum { FSTAT_MIXED = 0, /* FP64 timing/phases, FP32 resample/FFT/2F        */
 enum { FSTAT_C64 = 0,  /* interleaved float  (re, im) */
        FSTAT_C128 = 1  /* interleaved double (re, im) */ };
 
+/* Step-(v) interpolation kernel W(x), taps k0-D..k0+D, W(0) = 1 (Sec. 3
+ * says only "interpolating"; these are the readings offered):
+ *   FSTAT_INTERP_TAPERED    sin(pi x)/(N sin(pi x/N)) (0.54 + 0.46 cos(pi x/(D+1)))
+ *   FSTAT_INTERP_UNTAPERED  sin(pi x)/(N sin(pi x/N))
+ *   FSTAT_INTERP_PERIODIC   sin(pi x)/(M sin(pi x/M)), M = 2D + 1            */
+enum { FSTAT_INTERP_TAPERED = 0, FSTAT_INTERP_UNTAPERED = 1, FSTAT_INTERP_PERIODIC = 2 };
+
 /* Interferometer site: geodetic latitude, longitude (east positive) and the
  * angle gamma of the arm bisector, counter-clockwise from local East.  The
  * antenna patterns a(t), b(t) are those of Jaranowski, Krolak & Schutz (1998)
@@ -78,7 +85,7 @@ typedef struct {
   int32_t n_det;      /* 1..FSTAT_MAX_DET                                    */
   int32_t dterms;     /* interpolation half-width D (taps k0-D..k0+D), 1..32 */
   int32_t precision;  /* FSTAT_MIXED or FSTAT_FP64                           */
-  int32_t reserved;   /* must be 0                                           */
+  int32_t interp;     /* FSTAT_INTERP_* (0 = tapered Dirichlet)              */
   fstat_detector det[FSTAT_MAX_DET];
   double t0, dt;      /* first sample time, sample spacing (> 0)            */
   int64_t n_samples;  /* N, 1..2^24-1                                        */

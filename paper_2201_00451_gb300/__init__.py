@@ -35,6 +35,7 @@ ERR = {
 }
 MIXED, FP64 = 0, 1
 C64, C128 = 0, 1
+INTERP_TAPERED, INTERP_UNTAPERED, INTERP_PERIODIC = 0, 1, 2
 
 # Every symbol include/fstat.h declares (checked by the tests).
 EXPORTS = (
@@ -71,7 +72,7 @@ class Ephemeris(ctypes.Structure):
 class PlanDesc(ctypes.Structure):
     _fields_ = [
         ("n_det", ctypes.c_int32), ("dterms", ctypes.c_int32), ("precision", ctypes.c_int32),
-        ("reserved", ctypes.c_int32), ("det", Detector * MAX_DET), ("t0", ctypes.c_double),
+        ("interp", ctypes.c_int32), ("det", Detector * MAX_DET), ("t0", ctypes.c_double),
         ("dt", ctypes.c_double), ("n_samples", ctypes.c_int64), ("f_het", ctypes.c_double),
         ("n_fft", ctypes.c_int64), ("t_ref", ctypes.c_double), ("ephem", Ephemeris),
     ]
@@ -169,14 +170,14 @@ def _stream_handle(stream):
 
 
 def make_desc(*, detectors, t0, dt, n_samples, f_het, n_fft, dterms=8, precision=MIXED,
-              t_ref=float("nan"), ephemeris) -> PlanDesc:
+              t_ref=float("nan"), ephemeris, interp=INTERP_TAPERED) -> PlanDesc:
     """Fill a PlanDesc.  ``detectors``: objects with lat, lon, gamma (rad);
     ``ephemeris``: mapping with the fstat_ephemeris fields."""
     d = PlanDesc()
     d.n_det = len(detectors)
     d.dterms = int(dterms)
     d.precision = int(precision)
-    d.reserved = 0
+    d.interp = int(interp)
     for X, det in enumerate(detectors):
         d.det[X] = Detector(det.lat, det.lon, det.gamma)
     d.t0, d.dt, d.n_samples = float(t0), float(dt), int(n_samples)
@@ -213,13 +214,17 @@ class FstatPlan:
         self.n_samples = int(desc.n_samples)
 
     @classmethod
-    def from_target(cls, target, precision=MIXED, dterms=None):
+    def from_target(cls, target, precision=MIXED, dterms=None, interp=None):
         """Plan for an object exposing the workload fields (detectors, t0, dt,
-        n_samples, f_het, n_fft, dterms, t_ref, ephemeris)."""
+        n_samples, f_het, n_fft, dterms, t_ref, ephemeris; interp optional).
+        ``dterms`` / ``interp`` override the target's."""
+        if interp is None:
+            interp = getattr(target, "interp", INTERP_TAPERED)
         return cls(make_desc(detectors=target.detectors, t0=target.t0, dt=target.dt,
                              n_samples=target.n_samples, f_het=target.f_het, n_fft=target.n_fft,
                              dterms=target.dterms if dterms is None else dterms,
-                             precision=precision, t_ref=target.t_ref, ephemeris=target.ephemeris))
+                             precision=precision, t_ref=target.t_ref, ephemeris=target.ephemeris,
+                             interp=interp))
 
     # -- lifetime
     def close(self):

@@ -49,6 +49,7 @@ struct Geo {
   double t0, dt, f_het, t_ref;
   int64_t n;                           // samples per detector
   int n_det, dterms;
+  int interp;                          // FSTAT_INTERP_*
 };
 
 // ---------------------------------------------------- pair of complex values
@@ -126,8 +127,9 @@ struct TwiddleTables {
 TwiddleTables twiddle_layout(int precision, int log2n1, int log2n2, void* base);
 cudaError_t build_twiddles(int precision, int log2n1, int log2n2, void* base, cudaStream_t st);
 
-// Peaks mode of pass B: the 2F of one template is reduced in the kernel
-// instead of being written bin by bin (fstat_compute_peaks).
+// Arguments of pass B's other epilogues: peaks mode reduces one template's
+// 2F in the kernel instead of writing it bin by bin (fstat_compute_peaks);
+// accumulate mode adds it to a row at a bin offset (fstat_semicoherent).
 struct PeakArgs {
   unsigned long long* band_key;  // this template's row of band keys, or nullptr
   fstat_peak* peaks;             // crossing list [cap]
@@ -136,6 +138,7 @@ struct PeakArgs {
   long long tmpl;                // template index stored with each crossing
   float thr;
   int log2_band;                 // log2(bins per band)
+  int shift;                     // accumulate: bin m adds to bin m - shift
 };
 
 // Band key: order-preserving image of the float 2F in the high word, the
@@ -166,6 +169,11 @@ cudaError_t launch_pass_b_peak_f32(int log2_n1, int cb, int vb, const void* Z, i
                                    const SkyConst* sky, const PeakArgs& pk, cudaStream_t st);
 cudaError_t launch_pass_b_peak_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                                    const SkyConst* sky, const PeakArgs& pk, cudaStream_t st);
+// Accumulate mode: out[m - shift] += 2F[m] for 0 <= m - shift < n_fft.
+cudaError_t launch_pass_b_acc_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
+                                  const SkyConst* sky, float* out, int shift, cudaStream_t st);
+cudaError_t launch_pass_b_acc_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
+                                  const SkyConst* sky, float* out, int shift, cudaStream_t st);
 // Band keys of n rows x n_bands -> maximum 2F and its bin (band_bin may be null).
 cudaError_t launch_band_decode(const unsigned long long* keys, int64_t count, float* band_max,
                                int32_t* band_bin, cudaStream_t st);

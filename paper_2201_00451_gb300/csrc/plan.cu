@@ -248,7 +248,7 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   *out = nullptr;
   const fstat_plan_desc& d = *desc;
   if (d.n_det < 1 || d.n_det > FSTAT_MAX_DET || d.dterms < 1 || d.dterms > 32 ||
-      (d.precision != FSTAT_MIXED && d.precision != FSTAT_FP64) || d.reserved != 0 ||
+      (d.precision != FSTAT_MIXED && d.precision != FSTAT_FP64) || d.interp < FSTAT_INTERP_TAPERED || d.interp > FSTAT_INTERP_PERIODIC ||
       !(d.dt > 0.0) || !std::isfinite(d.t0) || !std::isfinite(d.f_het) || d.n_samples < 1 ||
       d.n_samples >= (int64_t(1) << 24) || !(d.ephem.c > 0.0))
     return FSTAT_ERR_INVALID_ARG;
@@ -291,6 +291,7 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   g.n = d.n_samples;
   g.n_det = d.n_det;
   g.dterms = d.dterms;
+  g.interp = d.interp;
 
   const int64_t N = d.n_samples;
   const size_t zb = d.precision == FSTAT_FP64 ? 16 : 8;

@@ -145,15 +145,23 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
         T d = (T)dl, sd, cd_;
         sincospi_t(d, &sd, &cd_);
         const T inv_taper = (T)1 / (T)(D + 1);
+        // Dirichlet kernel of the full series (length N) or of the 2D + 1
+        // taps themselves; the Hamming taper only for the default kernel
+        const T len = g.interp == FSTAT_INTERP_PERIODIC ? (T)(2 * D + 1) : nT;
+        const bool taper = g.interp == FSTAT_INTERP_TAPERED;
         for (int m = -D; m <= D; ++m) {
           long long k = k0 + m;
           if (k < 0 || k >= g.n) continue;
           T x = d - (T)m;
-          T sx, cx, st, ct;
-          sincospi_t(x / nT, &sx, &cx);
-          sincospi_t(x * inv_taper, &st, &ct);
+          T sx, cx;
+          sincospi_t(x / len, &sx, &cx);
           T num = (m & 1) ? -sd : sd;  // sin(pi (d - m)) = (-1)^m sin(pi d)
-          T wgt = num / (nT * sx) * ((T)0.54 + (T)0.46 * ct);
+          T wgt = num / (len * sx);
+          if (taper) {
+            T st, ct;
+            sincospi_t(x * inv_taper, &st, &ct);
+            wgt *= (T)0.54 + (T)0.46 * ct;
+          }
           TZ v = zx[k];
           zr += (T)v.x * wgt;
           zi += (T)v.y * wgt;

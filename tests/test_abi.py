@@ -58,7 +58,7 @@ def _desc(**over):
 @pytest.mark.parametrize("field,value,code", [
     ("n_det", 0, -1), ("n_det", 5, -1), ("dterms", 0, -1), ("precision", 7, -1),
     ("dt", 0.0, -1), ("n_samples", 0, -1), ("n_fft", 3000, -1), ("n_samples", 5000, -1),
-    ("n_fft", 1 << 25, -7), ("n_fft", 1 << 9, -7), ("reserved", 1, -1),
+    ("n_fft", 1 << 25, -7), ("n_fft", 1 << 9, -7), ("interp", 3, -1), ("interp", -1, -1),
 ])
 def test_plan_create_rejects_bad_descriptions(lib, field, value, code):
     d = _desc(**{field: value})
