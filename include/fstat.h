@@ -172,6 +172,25 @@ typedef struct {
 int fstat_compute_peaks(fstat_plan* plan, const fstat_template* tmpl, int64_t n_tmpl,
                         const fstat_peak_out* out, void* stream);
 
+/* Semi-coherent sum over segments (Sec. 6: the data are split into segments
+ * of about ten days, each searched with the F-statistic, and the segments'
+ * 2F summed, all on the GPU).  seg[0..n_seg) are plans over consecutive
+ * segments of one data set, sharing precision, dt, f_het and n_fft (their
+ * own n_samples, t0, t_ref, detectors and data).  Each HOST template
+ * (alpha, delta, f1dot, f2dot) has its spindowns at the global reference
+ * time t_ref, and output bin m is the frequency f_m = f_het + (m - n_fft/2)
+ * df at t_ref.  Segment s (offset D = t_ref,s - t_ref) is searched with
+ * f1dot + f2dot D and f2dot, and its bin m + k_s, k_s = rint((f1dot D +
+ * f2dot D^2/2) / df), is added to output bin m (nearest-bin sliding; terms
+ * outside the band add nothing):
+ *   twoF[i][m] = sum_s 2F_s[i][m + k_s]      (DEVICE, n_tmpl x n_fft floats)
+ * The work is enqueued on `stream` and on the first plan's side streams.
+ * Errors: INVALID_ARG (mismatched or repeated plans, n_seg outside
+ * 1..FSTAT_MAX_SEGMENTS, non-finite t_ref), NOT_READY, OOM, CUDA. */
+#define FSTAT_MAX_SEGMENTS 1024
+int fstat_semicoherent(fstat_plan* const* seg, int n_seg, const fstat_template* tmpl, int64_t n_tmpl,
+                       double t_ref, float* twoF, void* stream);
+
 /* 2F and its gradient at arbitrary (off-grid) parameters, for refinement.
  * For each candidate, eq. (Fstat) is evaluated with the demodulation
  * integrals of eqs. (Fa_DET)/(Fb_DET) (Sec. 2) summed directly over the

@@ -45,7 +45,7 @@ EXPORTS = (
     "fstat_strerror", "fstat_twoF_noalloc", "fstat_get_cta", "fstat_set_cta", "fstat_autotune",
     "fstat_grad", "fstat_batch_create", "fstat_batch_add", "fstat_batch_instantiate",
     "fstat_batch_launch", "fstat_batch_nodes", "fstat_batch_destroy", "fstat_set_streams",
-    "fstat_compute_peaks",
+    "fstat_compute_peaks", "fstat_semicoherent",
 )
 
 
@@ -139,6 +139,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fstat_batch_destroy": (None, [P]),
         "fstat_set_streams": (i32, [P, i32]),
         "fstat_compute_peaks": (i32, [P, P, i64, ctypes.POINTER(PeakOut), P]),
+        "fstat_semicoherent": (i32, [ctypes.POINTER(P), i32, P, i64, dbl, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -389,6 +390,26 @@ class FstatPlan:
     def autotune(self, stream=None):
         """fstat_autotune: pick the fastest FFT split and CTA shapes."""
         _check(self._lib.fstat_autotune(self._p, _stream_handle(stream)), "fstat_autotune")
+
+
+def semicoherent(plans, templates, t_ref: float, out=None, stream=None):
+    """fstat_semicoherent: sum over segment plans of 2F with nearest-bin
+    sliding, for templates whose spindowns are given at ``t_ref``.  Returns
+    a CUDA float32 tensor [n_templates, n_fft] (``out`` may supply it)."""
+    import torch
+    lib = load()
+    t = as_templates(templates)
+    n = len(t)
+    n_fft = plans[0].n_fft
+    if out is None:
+        out = torch.empty((n, n_fft), dtype=torch.float32, device="cuda")
+    if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() or out.numel() < n * n_fft:
+        raise ValueError("out must be a contiguous CUDA float32 tensor with n_templates*n_fft elements")
+    arr = (ctypes.c_void_p * len(plans))(*[p._p.value for p in plans])
+    rc = lib.fstat_semicoherent(arr, len(plans), ctypes.c_void_p(t.ctypes.data), n, float(t_ref),
+                                ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
+    _check(rc, "fstat_semicoherent")
+    return out
 
 
 def peaks_to_numpy(out) -> np.ndarray:

@@ -12,7 +12,7 @@ cudaError_t launch_pass_a_f64(int log2_n2, int ca, int va, const void* G, int64_
 cudaError_t launch_pass_b_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                               const SkyConst* sky, float* out, cudaStream_t st, const PeakArgs* pk) {
   if (pk) return launch_pass_b_peak_f64(log2_n1, cb, vb, Z, n2, twB, sky, *pk, st);
-  return fft::dispatch_b<double, false>(log2_n1, cb, vb, Z, n2, twB, sky, out, PeakArgs{}, st);
+  return fft::dispatch_b<double, fft::kStore>(log2_n1, cb, vb, Z, n2, twB, sky, out, PeakArgs{}, st);
 }
 
 }  // namespace fstat

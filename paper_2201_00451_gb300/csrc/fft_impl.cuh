@@ -102,6 +102,8 @@ template <typename T, int L, int C, int V = 0> struct Buf {
 // global memory once, when every band spans whole output rows (then each
 // band's bins in a tile sit in the same threads in every tile).
 constexpr int kPeakBands = 1024;
+// pass-B epilogues: store 2F, reduce it (peaks), add it to a shifted row
+constexpr int kStore = 0, kPeaks = 1, kAccumulate = 2;
 template <typename T, int L, int C, int V> struct PeakSmem {
   static constexpr size_t EXTRA = (size_t)kPeakBands * sizeof(unsigned long long);
   static constexpr bool ACC = kPipeline && Buf<T, L, C, V>::BYTES + EXTRA <= 227 * 1024;
@@ -533,7 +535,7 @@ __device__ __forceinline__ void peak_epilogue(const float* sf, int k2_0, int n2,
   }
 }
 
-template <typename T, int L, int CB, int V, bool STAGED, bool PEAK>
+template <typename T, int L, int CB, int V, bool STAGED, int MODE>
 __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type* buf, int c, int t,
                                             const typename PairMem<T>::type* __restrict__ Z, int n2,
                                             const typename TwT<T>::type* __restrict__ twL, T kA, T kB, T kC,
@@ -541,6 +543,20 @@ __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type*
                                             unsigned long long* ks) {
   using S = Shape<T, L, V>;
   const int k2 = tile * CB + c;
+  constexpr int NB = S::R0 / S::RL;
+  // accumulate mode: the running sums this thread adds to, loaded before
+  // the transform so their latency hides under it
+  float acc[MODE == kAccumulate ? S::R0 : 1];
+  if constexpr (MODE == kAccumulate) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+      for (int s = 0; s < S::RL; ++s) {
+        const int r = (t + q * S::TPC + s * S::NSL + L / 2) & (L - 1);
+        const int mg = k2 + n2 * r - pk.shift;
+        acc[q * S::RL + s] = (unsigned)mg < (unsigned)(n2 * L) ? out[mg] : 0.f;
+      }
+  }
   Pair<T> v[S::R0];
 #pragma unroll
   for (int s = 0; s < S::R0; ++s)
@@ -551,9 +567,8 @@ __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type*
   store_pass0<T, L, V, CB>(v, buf, t);
   passes<T, L, V, CB, 1, kPassBTable && sizeof(T) == 4>(v, buf, t, twL);
 
-  constexpr int NB = S::R0 / S::RL;
   float* sf = reinterpret_cast<float*>(buf - c);  // the CTA's stage, reused by the peaks epilogue
-  if constexpr (PEAK) __syncthreads();            // every thread is done with the exchange buffer
+  if constexpr (MODE == kPeaks) __syncthreads();  // every thread is done with the exchange buffer
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int b = t + q * S::TPC;
@@ -566,20 +581,24 @@ __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type*
       T re = x.ar * x.br + x.ai * x.bi;
       T tf = kB * fa2 + kA * fb2 - kC * re;
       const int r = (k1 + L / 2) & (L - 1);
-      if constexpr (PEAK) {
+      if constexpr (MODE == kPeaks) {
         sf[r * CB + c] = (float)tf;
+      } else if constexpr (MODE == kAccumulate) {
+        // semi-coherent sum: this segment's bin m adds to global bin m - shift
+        const int mg = k2 + n2 * r - pk.shift;
+        if ((unsigned)mg < (unsigned)(n2 * L)) out[mg] = acc[q * S::RL + s] + (float)tf;
       } else {
         __stcs(out + k2 + n2 * r, (float)tf);  // streaming store: keep G and Z in L2
       }
     }
   }
-  if constexpr (PEAK) {
+  if constexpr (MODE == kPeaks) {
     __syncthreads();
     peak_epilogue<CB, L * CB / (CB * S::TPC)>(sf, tile * CB, n2, pk, ks);
   }
 }
 
-template <typename T, int L, int CB, int V, bool PEAK>
+template <typename T, int L, int CB, int V, int MODE>
 __global__ void __launch_bounds__(CB * Shape<T, L, V>::TPC, (min_blocks<T, L, CB, V>()))
 k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
          const typename TwT<T>::type* __restrict__ twL, const SkyConst* __restrict__ sky,
@@ -597,7 +616,7 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
   // peaks mode with whole-row bands: this CTA's band keys in shared memory
   unsigned long long* ks = nullptr;
   int n_bands = 0;
-  if constexpr (PEAK && PeakSmem<T, L, CB, V>::ACC) {
+  if constexpr (MODE == kPeaks && PeakSmem<T, L, CB, V>::ACC) {
     if (pk.band_key && pk.log2_band >= 31 - __clz(n2)) {
       n_bands = (L * n2) >> pk.log2_band;
       if (n_bands <= kPeakBands) {
@@ -608,7 +627,7 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
     }
   }
   if constexpr (!kPipeline) {
-    pass_b_tile<T, L, CB, V, false, PEAK>(blockIdx.x, smem + c, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks);
+    pass_b_tile<T, L, CB, V, false, MODE>(blockIdx.x, smem + c, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks);
   } else {
     const int n_tiles = n2 / CB;
     auto stage = [&](int it) { return smem + (B::NBUF == 2 ? (it & 1) : 0) * (CB * S::LP) + c; };
@@ -637,10 +656,10 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
         cp_async_wait<0>();
       }
       __syncthreads();
-      pass_b_tile<T, L, CB, V, true, PEAK>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks);
+      pass_b_tile<T, L, CB, V, true, MODE>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks);
       __syncthreads();  // this buffer is the prefetch target two tiles on
     }
-    if constexpr (PEAK) {
+    if constexpr (MODE == kPeaks) {
       if (ks) {  // the loop ended on a barrier: every tile's keys are in
         for (int b = threadIdx.x; b < n_bands; b += blockDim.x)
           if (ks[b]) atomicMax(pk.band_key + b, ks[b]);
@@ -686,23 +705,23 @@ cudaError_t run_a(const void* G, int64_t lc, int64_t n, int n1, const void* twA,
   return cudaGetLastError();
 }
 
-template <typename T, int L, int CB, int V, bool PEAK>
+template <typename T, int L, int CB, int V, int MODE>
 cudaError_t run_b(const void* Z, int n2, const void* twB, const SkyConst* sky, float* out, const PeakArgs& pk,
                   cudaStream_t st) {
   using S = Shape<T, L, V>;
-  constexpr size_t smem = PEAK ? PeakSmem<T, L, CB, V>::BYTES : Buf<T, L, CB, V>::BYTES;
+  constexpr size_t smem = MODE == kPeaks ? PeakSmem<T, L, CB, V>::BYTES : Buf<T, L, CB, V>::BYTES;
   constexpr int threads = CB * S::TPC;
-  static_assert(!PEAK || (L * CB * sizeof(float) <= Buf<T, L, CB, V>::ONE), "peaks epilogue reuses the stage");
-  static_assert(!PEAK || threads % 32 == 0, "peaks epilogue works on whole warps");
+  static_assert(MODE != kPeaks || (L * CB * sizeof(float) <= Buf<T, L, CB, V>::ONE), "peaks epilogue reuses the stage");
+  static_assert(MODE != kPeaks || threads % 32 == 0, "peaks epilogue works on whole warps");
   static int ctas = 0;
   if (!ctas) {
-    cudaError_t e = resident_ctas(k_pass_b<T, L, CB, V, PEAK>, threads, smem, &ctas);
+    cudaError_t e = resident_ctas(k_pass_b<T, L, CB, V, MODE>, threads, smem, &ctas);
     if (e != cudaSuccess) return e;
   }
   if (n2 % CB) return cudaErrorInvalidConfiguration;
   const int tiles = n2 / CB;
   const int grid = (!kPipeline || tiles < ctas) ? tiles : ctas;
-  k_pass_b<T, L, CB, V, PEAK><<<grid, threads, smem, st>>>(
+  k_pass_b<T, L, CB, V, MODE><<<grid, threads, smem, st>>>(
       (const typename S::PM*)Z, n2, (const typename S::TW*)twB, sky, out, pk);
   return cudaGetLastError();
 }
@@ -739,29 +758,29 @@ cudaError_t pick_a(int ca, int v, const void* G, int64_t lc, int64_t n, int n1, 
   return cudaErrorInvalidConfiguration;
 }
 
-template <typename T, int L, int V, bool PEAK>
+template <typename T, int L, int V, int MODE>
 cudaError_t pick_b_v(int cb, const void* Z, int n2, const void* twB, const SkyConst* sky, float* out,
                      const PeakArgs& pk, cudaStream_t st) {
   switch (cb) {
-    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_b<T, L, 1, V, PEAK>(Z, n2, twB, sky, out, pk, st); break;
-    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_b<T, L, 2, V, PEAK>(Z, n2, twB, sky, out, pk, st); break;
-    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_b<T, L, 4, V, PEAK>(Z, n2, twB, sky, out, pk, st); break;
-    case 8: if constexpr (cfg_ok<T, L, 8, V>()) return run_b<T, L, 8, V, PEAK>(Z, n2, twB, sky, out, pk, st); break;
+    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_b<T, L, 1, V, MODE>(Z, n2, twB, sky, out, pk, st); break;
+    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_b<T, L, 2, V, MODE>(Z, n2, twB, sky, out, pk, st); break;
+    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_b<T, L, 4, V, MODE>(Z, n2, twB, sky, out, pk, st); break;
+    case 8: if constexpr (cfg_ok<T, L, 8, V>()) return run_b<T, L, 8, V, MODE>(Z, n2, twB, sky, out, pk, st); break;
     default: break;
   }
   return cudaErrorInvalidConfiguration;
 }
 
-template <typename T, int L, bool PEAK>
+template <typename T, int L, int MODE>
 cudaError_t pick_b(int cb, int v, const void* Z, int n2, const void* twB, const SkyConst* sky, float* out,
                    const PeakArgs& pk, cudaStream_t st) {
   using S = Shape<T, L, 0>;
   if (cb <= 0) cb = S::CB_DEF;
-  if (v == 0 && cb == S::CB_DEF) return run_b<T, L, S::CB_DEF, 0, PEAK>(Z, n2, twB, sky, out, pk, st);
+  if (v == 0 && cb == S::CB_DEF) return run_b<T, L, S::CB_DEF, 0, MODE>(Z, n2, twB, sky, out, pk, st);
   if constexpr (sizeof(T) == 4 && wide_variants<L>()) {
-    if (v == 0) return pick_b_v<T, L, 0, PEAK>(cb, Z, n2, twB, sky, out, pk, st);
+    if (v == 0) return pick_b_v<T, L, 0, MODE>(cb, Z, n2, twB, sky, out, pk, st);
     if constexpr (L >= 1024)
-      if (v == 1) return pick_b_v<T, L, 1, PEAK>(cb, Z, n2, twB, sky, out, pk, st);
+      if (v == 1) return pick_b_v<T, L, 1, MODE>(cb, Z, n2, twB, sky, out, pk, st);
   }
   return cudaErrorInvalidConfiguration;
 }
@@ -785,11 +804,11 @@ cudaError_t dispatch_a(int log2_n2, int ca, int v, const void* G, int64_t lc, in
   }
 }
 
-template <typename T, bool PEAK>
+template <typename T, int MODE>
 cudaError_t dispatch_b(int log2_n1, int cb, int v, const void* Z, int n2, const void* twB, const SkyConst* sky,
                        float* out, const PeakArgs& pk, cudaStream_t st) {
   switch (log2_n1) {
-    FSTAT_LEN_CASES(pick_b, , PEAK>(cb, v, Z, n2, twB, sky, out, pk, st))
+    FSTAT_LEN_CASES(pick_b, , MODE>(cb, v, Z, n2, twB, sky, out, pk, st))
     default: return cudaErrorInvalidValue;
   }
 }

@@ -225,6 +225,13 @@ cudaError_t launch_b(fstat_plan* p, int cb, int vb, float* out, cudaStream_t st,
       : launch_pass_b_f32(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk);
 }
 
+cudaError_t launch_b_acc(fstat_plan* p, float* out, int shift, cudaStream_t st, void* Z) {
+  const TwiddleTables& t = p->tt;
+  return p->d.precision == FSTAT_FP64
+      ? launch_pass_b_acc_f64(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st)
+      : launch_pass_b_acc_f32(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -492,6 +499,97 @@ int fstat_compute(fstat_plan* p, const fstat_template* tmpl, int64_t n_tmpl, flo
                        false, p->prof);
   if (rc) return rc;
   CK(cudaEventRecord(p->done, st));
+  return FSTAT_OK;
+}
+
+int fstat_semicoherent(fstat_plan* const* seg, int n_seg, const fstat_template* tmpl, int64_t n_tmpl,
+                       double t_ref, float* twoF, void* stream) {
+  if (!seg || n_seg < 1 || n_seg > FSTAT_MAX_SEGMENTS || !std::isfinite(t_ref) || (n_tmpl > 0 && !twoF))
+    return FSTAT_ERR_INVALID_ARG;
+  fstat_plan* p0 = seg[0];
+  for (int s = 0; s < n_seg; ++s) {
+    fstat_plan* p = seg[s];
+    if (!p || p->d.precision != p0->d.precision || p->d.dt != p0->d.dt || p->d.f_het != p0->d.f_het ||
+        p->d.n_fft != p0->d.n_fft)
+      return FSTAT_ERR_INVALID_ARG;
+    for (int r = 0; r < s; ++r)
+      if (seg[r] == p) return FSTAT_ERR_INVALID_ARG;
+    int rc = validate_templates(p, tmpl, n_tmpl);
+    if (rc) return rc;
+  }
+  if (n_tmpl == 0) return FSTAT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = n_tmpl, nfft = p0->d.n_fft;
+  const double df = 1.0 / ((double)nfft * p0->d.dt);
+  std::vector<int> ord(n);
+  sky_order(tmpl, n, ord.data());
+  // per segment: templates with f1dot carried to the segment's reference
+  // time, and the bin offset of its frequency axis (nearest bin)
+  std::vector<int> shift((size_t)n_seg * n);
+  int ns = fstat_plan::kMaxStreams;
+  for (int s = 0; s < n_seg; ++s) {
+    fstat_plan* p = seg[s];
+    int rc = ensure_capacity(p, n);
+    if (rc) return rc;
+    if (p->staged_pending) { CK(cudaEventSynchronize(p->staged)); p->staged_pending = false; }
+    const double d_ref = p->geo.t_ref - t_ref;
+    for (int64_t i = 0; i < n; ++i) {
+      fstat_template t = tmpl[i];
+      const double sh = std::rint((t.f1dot * d_ref + 0.5 * t.f2dot * d_ref * d_ref) / df);
+      if (!(std::fabs(sh) < 1e9)) return FSTAT_ERR_INVALID_ARG;
+      shift[(size_t)s * n + i] = (int)sh;
+      t.f1dot += t.f2dot * d_ref;
+      p->h_tmpl[i] = t;
+      p->h_order[i] = ord[i];
+    }
+    CK(cudaMemcpyAsync(p->d_tmpl, p->h_tmpl, (size_t)n * sizeof(fstat_template), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->d_order, p->h_order, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(p->staged, st));
+    p->staged_pending = true;
+    ns = std::min(ns, p->nstream);
+  }
+  CK(cudaMemsetAsync(twoF, 0, (size_t)n * nfft * sizeof(float), st));
+  // Templates rotate over the first plan's streams; every segment of one
+  // template runs on the same stream, so its additions to the output row
+  // are ordered, and each segment uses its own plan's intermediate for
+  // that stream.
+  int64_t i = 0;
+  while (i < n) {
+    const fstat_template& t0 = tmpl[ord[i]];
+    int64_t j = i + 1;
+    while (j < n && tmpl[ord[j]].alpha == t0.alpha && tmpl[ord[j]].delta == t0.delta) ++j;
+    for (int s = 0; s < n_seg; ++s) {
+      fstat_plan* p = seg[s];
+      if (!(p->sky_valid && p->sky_alpha == t0.alpha && p->sky_delta == t0.delta)) {
+        int rc = run_sky(p, t0.alpha, t0.delta, st);
+        if (rc) return rc;
+      }
+      launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, (int)i, (int)(j - i), p->d_coef, st);
+      CK(cudaGetLastError());
+    }
+    const int nq = (int)std::min<int64_t>(ns, j - i);
+    if (nq > 1) {
+      CK(cudaEventRecord(p0->fork, st));
+      for (int q = 1; q < nq; ++q) CK(cudaStreamWaitEvent(p0->side[q], p0->fork, 0));
+    }
+    for (int64_t k = i; k < j; ++k) {
+      const int q = (int)((k - i) % nq);
+      cudaStream_t sq = q ? p0->side[q] : st;
+      float* out = twoF + (int64_t)ord[k] * nfft;
+      for (int s = 0; s < n_seg; ++s) {
+        fstat_plan* p = seg[s];
+        cudaError_t e = launch_a(p, p->ca, p->va, p->d_coef + k, sq, p->Zs[q]);
+        if (e == cudaSuccess) e = launch_b_acc(p, out, shift[(size_t)s * n + ord[k]], sq, p->Zs[q]);
+        if (e != cudaSuccess) return cuda_status(e);
+      }
+    }
+    for (int q = 1; q < nq; ++q) {
+      CK(cudaEventRecord(p0->join[q], p0->side[q]));
+      CK(cudaStreamWaitEvent(st, p0->join[q], 0));
+    }
+    i = j;
+  }
+  for (int s = 0; s < n_seg; ++s) CK(cudaEventRecord(seg[s]->done, st));
   return FSTAT_OK;
 }
 
