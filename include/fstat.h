@@ -239,7 +239,8 @@ int fstat_set_split(fstat_plan* plan, int64_t n1);
  * rows per CTA of pass B (cb), 0 = default for the length; radix schedule
  * va / vb: 0 = radix-16 first, 1 = radix-8 first (lengths >= 1024).  A
  * shape that is not compiled for the current split makes fstat_compute
- * return FSTAT_ERR_CUDA. */
+ * return FSTAT_ERR_CUDA.  fstat_get_cta reports the shapes in effect (a
+ * default as its value for the current split). */
 int fstat_get_cta(const fstat_plan* plan, int* ca, int* va, int* cb, int* vb);
 int fstat_set_cta(fstat_plan* plan, int ca, int va, int cb, int vb);
 

@@ -23,6 +23,10 @@
 
 using namespace fstat;
 
+namespace fstat {
+int fft_default_c(int log2_len, int pass_b, int precision);  // fft_a_f32.cu
+}
+
 struct EventPair {
   cudaEvent_t a, b;
 };
@@ -796,9 +800,10 @@ int fstat_set_streams(fstat_plan* p, int n) {
 
 int fstat_get_cta(const fstat_plan* p, int* ca, int* va, int* cb, int* vb) {
   if (!p || !ca || !va || !cb || !vb) return FSTAT_ERR_INVALID_ARG;
-  *ca = p->ca;
+  // the shape the passes run with: 0 resolved to the length's default
+  *ca = p->ca > 0 ? p->ca : fft_default_c(p->log2n2, 0, p->d.precision);
   *va = p->va;
-  *cb = p->cb;
+  *cb = p->cb > 0 ? p->cb : fft_default_c(p->log2n1, 1, p->d.precision);
   *vb = p->vb;
   return FSTAT_OK;
 }
