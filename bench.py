@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-interp", action="store_true")
     ap.add_argument("--no-semicoh", action="store_true")
+    ap.add_argument("--no-skyheavy", action="store_true")
     ap.add_argument("--streams", type=int, default=2, help="template streams per plan (1..4)")
     ap.add_argument("--shape", default="", help="n1,ca,va,cb,vb: fixed FFT split and CTA shapes (skip autotune)")
     return ap.parse_args()
@@ -372,6 +373,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_large:
         line["large_search"] = large_bench(dev, stream)
 
+    # sky-dominated bank (many sky positions, few spindowns)
+    if rank == 0 and not args.no_skyheavy:
+        line["sky_heavy"] = sky_heavy_bench(t, xs, dev, stream, args)
+
     # semi-coherent search: ten 10-day segments summed on the device
     if rank == 0 and not args.no_semicoh:
         line["semicoherent"] = semicoh_bench(dev, stream, args)
@@ -632,6 +637,44 @@ def large_bench(dev, stream, n_tmpl=2048):
     return {"value": total / job_s, "unit": UNIT, "bins_per_s": total * t.n_fft / job_s,
             "sample": f"1 sky: per-sky work {ms_sky:.2f} ms + {len(tm)} templates at {per_t * 1e3:.1f} us each",
             "job_hours": job_s / 3600.0, "n_fft": t.n_fft, "n_samples": t.n_samples}
+
+
+def sky_heavy_bench(t, xs, dev, stream, args, n_sky=128, n_f1=11):
+    """A sky-dominated bank, shaped like the paper's pilot search (many sky
+    positions, 11 spindowns each, Sec. 5.3): the 10-day two-detector data,
+    128 sky positions in a 1 deg patch x 11 f1dot, per-sky work for every
+    sky position in every step."""
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+
+    rng = np.random.default_rng(77)
+    a0, d0 = t.skies[0]
+    skies = tuple((a0 + float(da), d0 + float(dd)) for da, dd in rng.uniform(-0.0087, 0.0087, (n_sky, 2)))
+    tm = pkg.as_templates(template_grid(skies, t.f1dots[-n_f1:], t.f2dots[:1]))
+    plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
+    for X in range(len(t.detectors)):
+        plan.set_data(X, xs[X], t.sigmas[X])
+    plan.autotune(stream)
+    out = torch.empty((len(tm), t.n_fft), dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        plan.compute_ptr(tm, out.data_ptr(), stream)
+    torch.cuda.synchronize(dev)
+    plan.set_profiling(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.invalidate_sky()
+        plan.compute_ptr(tm, out.data_ptr(), stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sec = e0.elapsed_time(e1) * 1e-3 / args.steps
+    n_sky_runs, ms_sky = plan.kernel_stats(2)
+    plan.close()
+    return {"value": len(tm) / sec, "unit": UNIT, "sky_positions_per_s": n_sky / sec,
+            "per_sky_ms": ms_sky / max(n_sky_runs, 1),
+            "workload": f"10-day H1+L1 data, {n_sky} sky positions x {n_f1} f1dot, FFT 2^22, "
+                        "per-sky work for every position in every step"}
 
 
 def refine_bench(t, xs, dev, n_cand=4096, steps=20):

@@ -17,6 +17,7 @@ constexpr int kMaxLog2 = 12;
 // Per-sky constants, written by k_sky_setup / k_sky_finalize (device memory).
 struct SkyConst {
   double alpha, delta;
+  double cos_alpha, sin_alpha;
   double nx, ny, nz;          // unit vector to the source
   double t_b0;                // start of the SSB grid
   double j_ref;               // (t_ref - t_b0) / dt
@@ -50,6 +51,15 @@ struct Geo {
   int64_t n;                           // samples per detector
   int n_det, dterms;
   int interp;                          // FSTAT_INTERP_*
+  double clon[kMaxDet], slon[kMaxDet]; // cos, sin of the longitudes
+  // Sky-independent timing table (sky.cu): cos, sin of the orbital phase and
+  // of the sidereal rotation angle at t = tab_t0 + i / tab_inv_h.
+  const double4* tab;
+  double tab_t0, tab_inv_h;
+  int tab_n;
+  // Roemer delay t_m of the current sky position for each detector on the
+  // same grid, [X * tab_n + i] (rewritten by every per-sky run)
+  double* tm_tab;
 };
 
 // ---------------------------------------------------- pair of complex values
@@ -104,6 +114,10 @@ __device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sin
 void launch_sky(const Geo& g, int precision, double alpha, double delta, const void* const* xh,
                 const int* xh_dtype, void* z, void* G, int n1, int64_t lc, double* partials,
                 int n_blocks, SkyConst* sky, int* err, cudaStream_t st);
+// Timing table: entries needed to cover [t_lo, t_hi] at spacing h, and the
+// kernel that fills them (FP64 sincos, once per plan).
+int time_table_entries(double t_lo, double t_hi, double h);
+cudaError_t launch_time_table(const Geo& g, double4* tab, cudaStream_t st);
 void launch_tmpl_coef(const SkyConst* sky, double dt, const fstat_template* tmpl,
                       const int* order, int first, int count, TmplCoef* out, cudaStream_t st);
 void launch_check_finite(const void* x, int dtype, int64_t n, int* err, cudaStream_t st);

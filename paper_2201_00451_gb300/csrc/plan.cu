@@ -27,6 +27,10 @@ namespace fstat {
 int fft_default_c(int log2_len, int pass_b, int precision);  // fft_a_f32.cu
 }
 
+namespace {
+constexpr double kTabStep = 30.0;  // s, spacing of the timing table
+}
+
 struct EventPair {
   cudaEvent_t a, b;
 };
@@ -57,6 +61,8 @@ struct fstat_plan {
   cudaEvent_t join[kMaxStreams] = {};
   double* partials = nullptr;
   int nblk = 0;
+  double4* tab = nullptr;        // timing table (geo.tab)
+  double* tm_tab = nullptr;      // per-sky Roemer delay table (geo.tm_tab)
   SkyConst* sky = nullptr;
   void* tw = nullptr;            // twiddle tables for the current split
   TwiddleTables tt{};
@@ -128,6 +134,8 @@ void free_all(fstat_plan* p) {
   }
   if (p->fork) cudaEventDestroy(p->fork);
   if (p->partials) cudaFree(p->partials);
+  if (p->tab) cudaFree(p->tab);
+  if (p->tm_tab) cudaFree(p->tm_tab);
   if (p->sky) cudaFree(p->sky);
   if (p->tw) cudaFree(p->tw);
   if (p->d_err) cudaFree(p->d_err);
@@ -293,6 +301,8 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
     g.gam[X] = d.det[X].gamma_rad;
     g.rcl[X] = d.ephem.r_earth * std::cos(d.det[X].lat_rad);
     g.rsl[X] = d.ephem.r_earth * std::sin(d.det[X].lat_rad);
+    g.clon[X] = std::cos(d.det[X].lon_rad);
+    g.slon[X] = std::sin(d.det[X].lon_rad);
     g.w[X] = 0.0;
   }
   g.t0 = d.t0;
@@ -317,6 +327,23 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
     e = cudaMalloc(&p->Zs[k], (size_t)d.n_fft * p->pair_bytes);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join[k], cudaEventDisableTiming);
+  }
+  // timing table over every epoch the timing can reach: the data span
+  // widened by the largest delay (|t_m| <= (au + r_earth)/c) plus margin
+  {
+    const double reach = (d.ephem.au + d.ephem.r_earth) / d.ephem.c + 100.0;
+    const double lo = d.t0 - 2.0 * reach - 2.0 * kTabStep;
+    const double hi = d.t0 + (double)N * d.dt + 2.0 * reach + 2.0 * kTabStep;
+    g.tab_n = time_table_entries(lo, hi, kTabStep);
+    g.tab_t0 = lo;
+    g.tab_inv_h = 1.0 / kTabStep;
+    double4* tab = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&tab, (size_t)g.tab_n * sizeof(double4));
+    p->tab = tab;
+    g.tab = tab;
+    if (e == cudaSuccess) e = cudaMalloc(&p->tm_tab, (size_t)g.tab_n * kMaxDet * sizeof(double));
+    g.tm_tab = p->tm_tab;
+    if (e == cudaSuccess) e = launch_time_table(g, tab, 0);
   }
   if (e == cudaSuccess) e = cudaMalloc(&p->partials, (size_t)3 * p->nblk * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->sky, sizeof(SkyConst));

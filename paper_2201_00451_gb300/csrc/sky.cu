@@ -9,6 +9,8 @@
 
 #include <math.h>
 
+#include <cmath>
+
 #include "fstat_internal.cuh"
 
 namespace fstat {
@@ -17,23 +19,95 @@ namespace {
 
 struct Rot { double c, s; };  // cos, sin of the detector's sidereal angle
 
-// Roemer delay t_m(t) = (r_orb + r_rot) . n / c  (Sec. 2 phase model).
-__device__ __forceinline__ double roemer(const Geo& g, const SkyConst& s, int X, double t, Rot* r) {
-  double so, co;
-  sincos(g.orb_ph0 + g.w_orb * t, &so, &co);
-  double orb = g.au * (co * s.nx + so * (g.cos_obl * s.ny + g.sin_obl * s.nz));
-  double sp, cp;
-  sincos(g.lon[X] + g.sid_ph0 + g.w_rot * t, &sp, &cp);
-  double rot = g.rcl[X] * (cp * s.nx + sp * s.ny) + g.rsl[X] * s.nz;
-  r->c = cp;
-  r->s = sp;
-  return (orb + rot) / g.c;
+// The orbital phase and the sidereal rotation angle enter the timing only
+// through their cosines and sines, which the plan tabulates every 30 s
+// (k_time_table, FP64 sincos once per entry) over the span the timing can
+// reach.  Per sky position the Roemer delay of each detector is then
+// tabulated at the same nodes (k_sky_table), and every timing evaluation
+// is the cubic Lagrange interpolation through the four nearest nodes.  The
+// interpolation error in t_m is ~1e-14 s (rotation term:
+// (w_rot h)^4 * 9/16/24 * R_E/c at h = 30 s), below the FP64 rounding of
+// t_m itself.
+struct TabPos {
+  int i;                      // first of the four nodes
+  double w0, w1, w2, w3;      // Lagrange weights
+};
+
+__device__ __forceinline__ TabPos tab_pos(const Geo& g, double t) {
+  const double x = (t - g.tab_t0) * g.tab_inv_h;
+  int i = (int)floor(x) - 1;                       // nodes i .. i + 3
+  i = i < 0 ? 0 : (i > g.tab_n - 4 ? g.tab_n - 4 : i);
+  const double f = x - (double)(i + 1);            // position from node i + 1
+  const double fm = f - 1.0, fp = f + 1.0, f2 = f - 2.0;
+  TabPos p;
+  p.i = i;
+  p.w0 = -f * fm * f2 * (1.0 / 6.0);
+  p.w1 = fp * fm * f2 * 0.5;
+  p.w2 = -fp * f * f2 * 0.5;
+  p.w3 = fp * f * fm * (1.0 / 6.0);
+  return p;
+}
+
+// Roemer delay t_m,X(t) of the current sky position (Sec. 2 phase model).
+__device__ __forceinline__ double tm_eval(const Geo& g, int X, double t) {
+  const TabPos p = tab_pos(g, t);
+  const double* v = g.tm_tab + (int64_t)X * g.tab_n + p.i;
+  return p.w0 * v[0] + p.w1 * v[1] + p.w2 * v[2] + p.w3 * v[3];
+}
+
+// t_m,X(t) and its derivative dt_m/dt (derivative of the same cubic)
+__device__ __forceinline__ double tm_eval_d(const Geo& g, int X, double t, double* dtm) {
+  const TabPos p = tab_pos(g, t);
+  const double f = (t - g.tab_t0) * g.tab_inv_h - (double)(p.i + 1);
+  const double f2 = f * f;
+  const double d0 = -(3.0 * f2 - 6.0 * f + 2.0) * (1.0 / 6.0);
+  const double d1 = (3.0 * f2 - 4.0 * f - 1.0) * 0.5;
+  const double d2 = -(3.0 * f2 - 2.0 * f - 2.0) * 0.5;
+  const double d3 = (3.0 * f2 - 1.0) * (1.0 / 6.0);
+  const double* v = g.tm_tab + (int64_t)X * g.tab_n + p.i;
+  *dtm = (d0 * v[0] + d1 * v[1] + d2 * v[2] + d3 * v[3]) * g.tab_inv_h;
+  return p.w0 * v[0] + p.w1 * v[1] + p.w2 * v[2] + p.w3 * v[3];
+}
+
+// cos, sin of detector X's sidereal angle lon + rotation angle at t
+__device__ __forceinline__ Rot rot_eval(const Geo& g, int X, double t) {
+  const TabPos p = tab_pos(g, t);
+  const double4 a = g.tab[p.i], b = g.tab[p.i + 1], c = g.tab[p.i + 2], d = g.tab[p.i + 3];
+  const double cq = p.w0 * a.z + p.w1 * b.z + p.w2 * c.z + p.w3 * d.z;
+  const double sq = p.w0 * a.w + p.w1 * b.w + p.w2 * c.w + p.w3 * d.w;
+  return Rot{g.clon[X] * cq - g.slon[X] * sq, g.slon[X] * cq + g.clon[X] * sq};
+}
+
+__global__ void k_time_table(Geo g, double4* __restrict__ tab) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.tab_n; i += gridDim.x * blockDim.x) {
+    const double t = g.tab_t0 + (double)i / g.tab_inv_h;
+    double so, co, sq, cq;
+    sincos(g.orb_ph0 + g.w_orb * t, &so, &co);
+    sincos(g.sid_ph0 + g.w_rot * t, &sq, &cq);
+    tab[i] = make_double4(co, so, cq, sq);
+  }
+}
+
+// t_m = (r_orb + r_rot) . n / c at every node, for every detector
+__global__ void k_sky_table(Geo g, const SkyConst* __restrict__ skyp) {
+  const SkyConst& s = *skyp;
+  const double py = g.cos_obl * s.ny + g.sin_obl * s.nz;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.tab_n; i += gridDim.x * blockDim.x) {
+    const double4 e = g.tab[i];
+    const double orb = g.au * (e.x * s.nx + e.y * py);
+    for (int X = 0; X < g.n_det; ++X) {
+      const double cp = g.clon[X] * e.z - g.slon[X] * e.w;
+      const double sp = g.slon[X] * e.z + g.clon[X] * e.w;
+      const double rot = g.rcl[X] * (cp * s.nx + sp * s.ny) + g.rsl[X] * s.nz;
+      g.tm_tab[(int64_t)X * g.tab_n + i] = (orb + rot) / g.c;
+    }
+  }
 }
 
 // a(t), b(t) from the harmonic coefficients and the sidereal angle (JKS 1998
 // eqs. 12-13): H = alpha - phi, h = (1, cos 2H, sin 2H, cos H, sin H).
 __device__ __forceinline__ void antenna(const SkyConst& s, int X, const Rot& r, double* a, double* b) {
-  double ca = cos(s.alpha), sa = sin(s.alpha);
+  const double ca = s.cos_alpha, sa = s.sin_alpha;
   double cH = ca * r.c + sa * r.s;
   double sH = sa * r.c - ca * r.s;
   double c2H = cH * cH - sH * sH;
@@ -47,8 +121,10 @@ __global__ void k_sky_setup(Geo g, double alpha, double delta, SkyConst* out) {
   SkyConst s;
   s.alpha = alpha;
   s.delta = delta;
-  s.nx = cos(delta) * cos(alpha);
-  s.ny = cos(delta) * sin(alpha);
+  s.cos_alpha = cos(alpha);
+  s.sin_alpha = sin(alpha);
+  s.nx = cos(delta) * s.cos_alpha;
+  s.ny = cos(delta) * s.sin_alpha;
   s.nz = sin(delta);
   // SSB grid start: t0 + orbital Roemer delay at the data midpoint
   double t_mid = g.t0 + 0.5 * (double)g.n * g.dt;
@@ -94,8 +170,7 @@ __global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* _
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < g.n;
        k += (int64_t)gridDim.x * blockDim.x) {
     double t = g.t0 + (double)k * g.dt;
-    Rot r;
-    double ph = g.f_het * roemer(g, s, X, t, &r);
+    double ph = g.f_het * tm_eval(g, X, t);
     ph -= floor(ph);
     TIn x = xh[k];
     const double is = g.inv_sigma_ref;
@@ -127,10 +202,17 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
     const int D = g.dterms;
     const T nT = (T)g.n;
     for (int X = 0; X < g.n_det; ++X) {
-      Rot r;
-      double T_ = tb - roemer(g, s, X, tb, &r);
-#pragma unroll 1
-      for (int it = 0; it < 3; ++it) T_ = tb - roemer(g, s, X, T_, &r);
+      // T + t_m(T) = t_b: the fixed-point start T0 = t_b - t_m(t_b), then one
+      // Newton step.  |dt_m/dT| ~ 1e-4 puts T0 within ~0.05 s of the root and
+      // |d2t_m/dT2| ~ 1e-10 /s the Newton step within ~1e-13 s of it, below
+      // the FP64 spacing of T (~1e-10 s at 1e6 s): the root three fixed-point
+      // iterations reach, with two timing evaluations instead of four.
+      double T_ = tb - tm_eval(g, X, tb);
+      {
+        double dtm;
+        const double tm = tm_eval_d(g, X, T_, &dtm);
+        T_ -= (T_ + tm - tb) / (1.0 + dtm);
+      }
       double u = (T_ - g.t0) / g.dt;
       long long k0 = __double2ll_rn(u);
       if (k0 < 0 || k0 > g.n - 1) continue;
@@ -168,7 +250,7 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
         }
       }
       double a, b;
-      antenna(s, X, r, &a, &b);
+      antenna(s, X, rot_eval(g, X, T_), &a, &b);
       double w = g.w[X];
       T wa = (T)(w * a), wb = (T)(w * b);
       acc.ar += wa * zr;
@@ -282,10 +364,21 @@ void launch_phase(const Geo& g, int X, const void* xh, void* z, const SkyConst* 
 
 }  // namespace
 
+int time_table_entries(double t_lo, double t_hi, double h) {
+  return (int)std::ceil((t_hi - t_lo) / h) + 1;
+}
+
+cudaError_t launch_time_table(const Geo& g, double4* tab, cudaStream_t st) {
+  const int blocks = (g.tab_n + 255) / 256;
+  k_time_table<<<blocks, 256, 0, st>>>(g, tab);
+  return cudaGetLastError();
+}
+
 void launch_sky(const Geo& g, int precision, double alpha, double delta, const void* const* xh,
                 const int* xh_dtype, void* z, void* G, int n1, int64_t lc, double* partials,
                 int n_blocks, SkyConst* sky, int* err, cudaStream_t st) {
   k_sky_setup<<<1, 32, 0, st>>>(g, alpha, delta, sky);
+  k_sky_table<<<(g.tab_n + 255) / 256, 256, 0, st>>>(g, sky);
   for (int X = 0; X < g.n_det; ++X) {
     bool in64 = xh_dtype[X] == FSTAT_C128;
     if (precision == FSTAT_FP64) {
