@@ -11,7 +11,7 @@ One template at a time, in the order the paper lists the steps:
       zero-padded to n_fft (eqs. Fa, Fb of Sec. 2)
 (vii) 2F = 2 (B |Fa|^2 + A |Fb|^2 - 2 C Re(Fa Fb*)) / D        (eq. Fstat)
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
 
 * sign of step (iii): with the phase model Phi = 2 pi f0 [t + t_m] of Sec. 2,
   demodulation by exp(-i Phi) in eqs. (Fa_DET)/(Fb_DET) and heterodyning by
@@ -20,8 +20,9 @@ Readings of points the paper leaves open (each is listed in the design doc):
   mirror-image heterodyne convention.  The brute-force pin decides.
 * SSB grid: t_b^0 = t_0 + (orbital Roemer delay at the data midpoint), the
   same n_samples and dt as the detector grid, so the grid covers the data.
-* interpolation kernel (Sec. 3 says only "interpolating"):
+* interpolation kernel (Sec. 3 says only "interpolating"), by default
       W(x) = sin(pi x) / (N sin(pi x / N)) * (0.54 + 0.46 cos(pi x / (D + 1)))
+  (untapered and periodic variants in dirichlet_weight),
   with N the detector sample count, W(0) = 1, taps k0 - D .. k0 + D with
   k0 = rint(u) (half to even), samples outside [0, N) count as zero, and the
   SSB point is valid for detector X iff 0 <= k0 <= N - 1.
