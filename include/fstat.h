@@ -244,7 +244,7 @@ int fstat_set_split(fstat_plan* plan, int64_t n1);
 int fstat_get_cta(const fstat_plan* plan, int* ca, int* va, int* cb, int* vb);
 int fstat_set_cta(fstat_plan* plan, int ca, int va, int cb, int vb);
 
-/* Number of streams (1..4, default 2) over which consecutive templates
+/* Number of streams (1..8; default 4 for n_fft <= 2^19, else 2) over which consecutive templates
  * rotate inside fstat_compute; each stream owns an n_fft-point intermediate
  * (16 B per point in FP32), so the FFT passes of consecutive templates
  * overlap.  Synchronises. */
