@@ -236,13 +236,21 @@ int fstat_get_split(const fstat_plan* plan, int64_t* n1, int64_t* n2);
 int fstat_set_split(fstat_plan* plan, int64_t n1);
 
 /* Launch shapes of the two FFT passes: columns per CTA of pass A (ca),
- * rows per CTA of pass B (cb), 0 = default for the length; radix schedule
- * va / vb: 0 = radix-16 first, 1 = radix-8 first (lengths >= 1024).  A
- * shape that is not compiled for the current split makes fstat_compute
- * return FSTAT_ERR_CUDA.  fstat_get_cta reports the shapes in effect (a
- * default as its value for the current split). */
+ * rows per CTA of pass B (cb), 0 = default for the length; schedule va /
+ * vb: bit 0 = radix-8 first (lengths >= 1024, else radix-16 first), bit 1 =
+ * one shared-memory buffer instead of two (no prefetch, half the shared
+ * memory).  A shape that is not compiled for the current split makes
+ * fstat_compute return FSTAT_ERR_CUDA.  fstat_get_cta reports the shapes
+ * in effect (a default as its value for the current split). */
 int fstat_get_cta(const fstat_plan* plan, int* ca, int* va, int* cb, int* vb);
 int fstat_set_cta(fstat_plan* plan, int ca, int va, int cb, int vb);
+
+/* Residency of the persistent FFT passes: at most ra (pass A) / rb (pass
+ * B) CTAs per SM, 0 = every CTA that fits (default).  With single-buffer
+ * shapes a cap lets one CTA of each pass share an SM while consecutive
+ * templates run on different streams.  Values 0..32. */
+int fstat_set_residency(fstat_plan* plan, int ra, int rb);
+int fstat_get_residency(const fstat_plan* plan, int* ra, int* rb);
 
 /* Number of streams (1..8; default 4 for n_fft <= 2^19, else 2) over which consecutive templates
  * rotate inside fstat_compute; each stream owns an n_fft-point intermediate

@@ -45,7 +45,7 @@ EXPORTS = (
     "fstat_strerror", "fstat_twoF_noalloc", "fstat_get_cta", "fstat_set_cta", "fstat_autotune",
     "fstat_grad", "fstat_batch_create", "fstat_batch_add", "fstat_batch_instantiate",
     "fstat_batch_launch", "fstat_batch_nodes", "fstat_batch_destroy", "fstat_set_streams",
-    "fstat_compute_peaks", "fstat_semicoherent",
+    "fstat_compute_peaks", "fstat_semicoherent", "fstat_set_residency", "fstat_get_residency",
 )
 
 
@@ -140,6 +140,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fstat_set_streams": (i32, [P, i32]),
         "fstat_compute_peaks": (i32, [P, P, i64, ctypes.POINTER(PeakOut), P]),
         "fstat_semicoherent": (i32, [ctypes.POINTER(P), i32, P, i64, dbl, P, P]),
+        "fstat_set_residency": (i32, [P, i32, i32]),
+        "fstat_get_residency": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -379,6 +381,16 @@ class FstatPlan:
         v = [ctypes.c_int() for _ in range(4)]
         _check(self._lib.fstat_get_cta(self._p, *[ctypes.byref(x) for x in v]), "fstat_get_cta")
         return tuple(x.value for x in v)
+
+    @property
+    def residency(self):
+        """(ra, rb): persistent CTAs per SM of pass A and pass B (0 = all that fit)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.fstat_get_residency(self._p, ctypes.byref(a), ctypes.byref(b)), "fstat_get_residency")
+        return a.value, b.value
+
+    def set_residency(self, ra: int, rb: int):
+        _check(self._lib.fstat_set_residency(self._p, int(ra), int(rb)), "fstat_set_residency")
 
     def set_cta(self, ca: int, cb: int, va: int = 0, vb: int = 0):
         _check(self._lib.fstat_set_cta(self._p, int(ca), int(va), int(cb), int(vb)), "fstat_set_cta")

@@ -4,9 +4,10 @@
 namespace fstat {
 
 cudaError_t launch_pass_b_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
-                              const SkyConst* sky, float* out, cudaStream_t st, const PeakArgs* pk) {
-  if (pk) return launch_pass_b_peak_f32(log2_n1, cb, vb, Z, n2, twB, sky, *pk, st);
-  return fft::dispatch_b<float, fft::kStore>(log2_n1, cb, vb, Z, n2, twB, sky, out, PeakArgs{}, st);
+                              const SkyConst* sky, float* out, cudaStream_t st, const PeakArgs* pk,
+                              int res) {
+  if (pk) return launch_pass_b_peak_f32(log2_n1, cb, vb, Z, n2, twB, sky, *pk, st, res);
+  return fft::dispatch_b<float, fft::kStore>(log2_n1, cb, vb, Z, n2, twB, sky, out, PeakArgs{}, st, res);
 }
 
 }  // namespace fstat

@@ -7,13 +7,13 @@
 namespace fstat {
 
 cudaError_t launch_pass_b_peak_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
-                                   const SkyConst* sky, const PeakArgs& pk, cudaStream_t st) {
-  return fft::dispatch_b<float, fft::kPeaks>(log2_n1, cb, vb, Z, n2, twB, sky, nullptr, pk, st);
+                                   const SkyConst* sky, const PeakArgs& pk, cudaStream_t st, int res) {
+  return fft::dispatch_b<float, fft::kPeaks>(log2_n1, cb, vb, Z, n2, twB, sky, nullptr, pk, st, res);
 }
 
 cudaError_t launch_pass_b_peak_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
-                                   const SkyConst* sky, const PeakArgs& pk, cudaStream_t st) {
-  return fft::dispatch_b<double, fft::kPeaks>(log2_n1, cb, vb, Z, n2, twB, sky, nullptr, pk, st);
+                                   const SkyConst* sky, const PeakArgs& pk, cudaStream_t st, int res) {
+  return fft::dispatch_b<double, fft::kPeaks>(log2_n1, cb, vb, Z, n2, twB, sky, nullptr, pk, st, res);
 }
 
 namespace {

@@ -5,14 +5,15 @@ namespace fstat {
 
 cudaError_t launch_pass_a_f64(int log2_n2, int ca, int va, const void* G, int64_t lc, int64_t n, int n1,
                               const void* twA, const void* hi, const void* lo, int h, const TmplCoef* coef,
-                              void* Z, cudaStream_t st) {
-  return fft::dispatch_a<double>(log2_n2, ca, va, G, lc, n, n1, twA, hi, lo, h, coef, Z, st);
+                              void* Z, cudaStream_t st, int res) {
+  return fft::dispatch_a<double>(log2_n2, ca, va, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
 }
 
 cudaError_t launch_pass_b_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
-                              const SkyConst* sky, float* out, cudaStream_t st, const PeakArgs* pk) {
-  if (pk) return launch_pass_b_peak_f64(log2_n1, cb, vb, Z, n2, twB, sky, *pk, st);
-  return fft::dispatch_b<double, fft::kStore>(log2_n1, cb, vb, Z, n2, twB, sky, out, PeakArgs{}, st);
+                              const SkyConst* sky, float* out, cudaStream_t st, const PeakArgs* pk,
+                              int res) {
+  if (pk) return launch_pass_b_peak_f64(log2_n1, cb, vb, Z, n2, twB, sky, *pk, st, res);
+  return fft::dispatch_b<double, fft::kStore>(log2_n1, cb, vb, Z, n2, twB, sky, out, PeakArgs{}, st, res);
 }
 
 }  // namespace fstat

@@ -52,9 +52,11 @@ template <> struct TwT<double> { using type = double2; };
 
 // ------------------------------------------------------------ radix schedule
 // V = 0: radix-16 first (fewest shared-memory passes, 16 points per thread);
-// V = 1 (lengths >= 1024): radix-8 first (8 points per thread, half the
-// registers, one more pass).  The first radix is the largest.
-__host__ __device__ constexpr bool r8(int L, int V) { return V == 1 && L >= 1024; }
+// Schedule code V: bit 0 (lengths >= 1024) = radix-8 first (8 points per
+// thread, half the registers, one more pass); bit 1 = one shared buffer
+// (no prefetch), half the shared memory, so that a CTA of each pass fits
+// on one SM.  The first radix is the largest.
+__host__ __device__ constexpr bool r8(int L, int V) { return (V & 1) && L >= 1024; }
 __host__ __device__ constexpr int np_of(int L, int V) { return r8(L, V) ? 4 : (L <= 256 ? 2 : 3); }
 __host__ __device__ constexpr int r_of(int L, int p, int V) {
   return r8(L, V)   ? (p < 3 ? 8 : L / 512)
@@ -93,7 +95,7 @@ template <typename T, int L, int V = 0> struct Shape {
 constexpr size_t kSmemCap = (size_t)220 * 1024;
 template <typename T, int L, int C, int V = 0> struct Buf {
   static constexpr size_t ONE = (size_t)C * Shape<T, L, V>::LP * sizeof(typename Shape<T, L, V>::PM);
-  static constexpr int NBUF = (kPipeline && 2 * ONE <= kSmemCap) ? 2 : 1;
+  static constexpr int NBUF = (kPipeline && !(V & 2) && 2 * ONE <= kSmemCap) ? 2 : 1;
   static constexpr size_t BYTES = NBUF * ONE;
 };
 
@@ -374,7 +376,7 @@ template <typename T, int L, int C, int V> constexpr int min_blocks() {
   // radix-8 variants: ask for enough resident CTAs to cap registers at 64
   constexpr int threads = C * Shape<T, L, V>::TPC;
   constexpr int want = 65536 / (threads * 64);
-  return (V == 1 && kR8MinBlocks > 0 && want > 1) ? want : 1;
+  return ((V & 1) && kR8MinBlocks > 0 && want > 1) ? want : 1;
 }
 
 // Direct mode (kPipeline = false): one tile per CTA.  Pipelined mode: the
@@ -672,7 +674,7 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
 // Resident CTAs of a persistent kernel: SM count x CTAs per SM (queried
 // once per kernel instantiation).
 template <typename K>
-cudaError_t resident_ctas(K kernel, int threads, size_t smem, int* out) {
+cudaError_t resident_ctas(K kernel, int threads, size_t smem, int* out, int* out_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -681,24 +683,34 @@ cudaError_t resident_ctas(K kernel, int threads, size_t smem, int* out) {
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   *out = sms * per_sm;
+  *out_per_sm = per_sm;
   return cudaSuccess;
+}
+
+// Persistent grid: every resident CTA, or at most `res` per SM (res > 0),
+// which leaves room on each SM for a CTA of the other pass of a
+// neighbouring template running on another stream.
+inline int persistent_grid(int tiles, int ctas, int per_sm, int res) {
+  int g = ctas;
+  if (res > 0 && res < per_sm) g = ctas / per_sm * res;
+  return (!kPipeline || tiles < g) ? tiles : g;
 }
 
 template <typename T, int L, int CA, int V>
 cudaError_t run_a(const void* G, int64_t lc, int64_t n, int n1, const void* twA, const void* hi,
-                  const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st) {
+                  const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st, int res) {
   using S = Shape<T, L, V>;
   constexpr size_t smem = Buf<T, L, CA, V>::BYTES;
   constexpr int threads = CA * S::TPC;
-  static int ctas = 0;
+  static int ctas = 0, per_sm = 0;
   if (!ctas) {
-    cudaError_t e = resident_ctas(k_pass_a<T, L, CA, V>, threads, smem, &ctas);
+    cudaError_t e = resident_ctas(k_pass_a<T, L, CA, V>, threads, smem, &ctas, &per_sm);
     if (e != cudaSuccess) return e;
   }
   if (n1 % CA) return cudaErrorInvalidConfiguration;
   const int tiles = n1 / CA;
   using TW = typename S::TW;
-  const int grid = (!kPipeline || tiles < ctas) ? tiles : ctas;
+  const int grid = persistent_grid(tiles, ctas, per_sm, res);
   k_pass_a<T, L, CA, V><<<grid, threads, smem, st>>>(
       (const typename S::PM*)G, lc, (int)n, n1, (const TW*)twA, coef, (typename S::PM*)Z);
   (void)hi; (void)lo; (void)h;
@@ -707,20 +719,20 @@ cudaError_t run_a(const void* G, int64_t lc, int64_t n, int n1, const void* twA,
 
 template <typename T, int L, int CB, int V, int MODE>
 cudaError_t run_b(const void* Z, int n2, const void* twB, const SkyConst* sky, float* out, const PeakArgs& pk,
-                  cudaStream_t st) {
+                  cudaStream_t st, int res) {
   using S = Shape<T, L, V>;
   constexpr size_t smem = MODE == kPeaks ? PeakSmem<T, L, CB, V>::BYTES : Buf<T, L, CB, V>::BYTES;
   constexpr int threads = CB * S::TPC;
   static_assert(MODE != kPeaks || (L * CB * sizeof(float) <= Buf<T, L, CB, V>::ONE), "peaks epilogue reuses the stage");
   static_assert(MODE != kPeaks || threads % 32 == 0, "peaks epilogue works on whole warps");
-  static int ctas = 0;
+  static int ctas = 0, per_sm = 0;
   if (!ctas) {
-    cudaError_t e = resident_ctas(k_pass_b<T, L, CB, V, MODE>, threads, smem, &ctas);
+    cudaError_t e = resident_ctas(k_pass_b<T, L, CB, V, MODE>, threads, smem, &ctas, &per_sm);
     if (e != cudaSuccess) return e;
   }
   if (n2 % CB) return cudaErrorInvalidConfiguration;
   const int tiles = n2 / CB;
-  const int grid = (!kPipeline || tiles < ctas) ? tiles : ctas;
+  const int grid = persistent_grid(tiles, ctas, per_sm, res);
   k_pass_b<T, L, CB, V, MODE><<<grid, threads, smem, st>>>(
       (const typename S::PM*)Z, n2, (const typename S::TW*)twB, sky, out, pk);
   return cudaGetLastError();
@@ -734,11 +746,11 @@ template <int L> constexpr bool wide_variants() { return L >= 512; }
 // shape code: c = columns (A) / rows (B) per CTA, 0 = default; v = schedule
 template <typename T, int L, int V>
 cudaError_t pick_a_v(int ca, const void* G, int64_t lc, int64_t n, int n1, const void* twA, const void* hi,
-                     const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st) {
+                     const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st, int res) {
   switch (ca) {
-    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_a<T, L, 1, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st); break;
-    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_a<T, L, 2, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st); break;
-    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_a<T, L, 4, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st); break;
+    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_a<T, L, 1, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res); break;
+    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_a<T, L, 2, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res); break;
+    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_a<T, L, 4, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res); break;
     default: break;
   }
   return cudaErrorInvalidConfiguration;
@@ -746,26 +758,29 @@ cudaError_t pick_a_v(int ca, const void* G, int64_t lc, int64_t n, int n1, const
 
 template <typename T, int L>
 cudaError_t pick_a(int ca, int v, const void* G, int64_t lc, int64_t n, int n1, const void* twA, const void* hi,
-                   const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st) {
+                   const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st, int res) {
   using S = Shape<T, L, 0>;
   if (ca <= 0) ca = S::CA_DEF;
-  if (v == 0 && ca == S::CA_DEF) return run_a<T, L, S::CA_DEF, 0>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st);
+  if (v == 0 && ca == S::CA_DEF) return run_a<T, L, S::CA_DEF, 0>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
   if constexpr (sizeof(T) == 4 && wide_variants<L>()) {
-    if (v == 0) return pick_a_v<T, L, 0>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st);
-    if constexpr (L >= 1024)
-      if (v == 1) return pick_a_v<T, L, 1>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st);
+    if (v == 0) return pick_a_v<T, L, 0>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
+    if (v == 2) return pick_a_v<T, L, 2>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
+    if constexpr (L >= 1024) {
+      if (v == 1) return pick_a_v<T, L, 1>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
+      if (v == 3) return pick_a_v<T, L, 3>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
+    }
   }
   return cudaErrorInvalidConfiguration;
 }
 
 template <typename T, int L, int V, int MODE>
 cudaError_t pick_b_v(int cb, const void* Z, int n2, const void* twB, const SkyConst* sky, float* out,
-                     const PeakArgs& pk, cudaStream_t st) {
+                     const PeakArgs& pk, cudaStream_t st, int res) {
   switch (cb) {
-    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_b<T, L, 1, V, MODE>(Z, n2, twB, sky, out, pk, st); break;
-    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_b<T, L, 2, V, MODE>(Z, n2, twB, sky, out, pk, st); break;
-    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_b<T, L, 4, V, MODE>(Z, n2, twB, sky, out, pk, st); break;
-    case 8: if constexpr (cfg_ok<T, L, 8, V>()) return run_b<T, L, 8, V, MODE>(Z, n2, twB, sky, out, pk, st); break;
+    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_b<T, L, 1, V, MODE>(Z, n2, twB, sky, out, pk, st, res); break;
+    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_b<T, L, 2, V, MODE>(Z, n2, twB, sky, out, pk, st, res); break;
+    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_b<T, L, 4, V, MODE>(Z, n2, twB, sky, out, pk, st, res); break;
+    case 8: if constexpr (cfg_ok<T, L, 8, V>()) return run_b<T, L, 8, V, MODE>(Z, n2, twB, sky, out, pk, st, res); break;
     default: break;
   }
   return cudaErrorInvalidConfiguration;
@@ -773,14 +788,17 @@ cudaError_t pick_b_v(int cb, const void* Z, int n2, const void* twB, const SkyCo
 
 template <typename T, int L, int MODE>
 cudaError_t pick_b(int cb, int v, const void* Z, int n2, const void* twB, const SkyConst* sky, float* out,
-                   const PeakArgs& pk, cudaStream_t st) {
+                   const PeakArgs& pk, cudaStream_t st, int res) {
   using S = Shape<T, L, 0>;
   if (cb <= 0) cb = S::CB_DEF;
-  if (v == 0 && cb == S::CB_DEF) return run_b<T, L, S::CB_DEF, 0, MODE>(Z, n2, twB, sky, out, pk, st);
+  if (v == 0 && cb == S::CB_DEF) return run_b<T, L, S::CB_DEF, 0, MODE>(Z, n2, twB, sky, out, pk, st, res);
   if constexpr (sizeof(T) == 4 && wide_variants<L>()) {
-    if (v == 0) return pick_b_v<T, L, 0, MODE>(cb, Z, n2, twB, sky, out, pk, st);
-    if constexpr (L >= 1024)
-      if (v == 1) return pick_b_v<T, L, 1, MODE>(cb, Z, n2, twB, sky, out, pk, st);
+    if (v == 0) return pick_b_v<T, L, 0, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
+    if (v == 2) return pick_b_v<T, L, 2, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
+    if constexpr (L >= 1024) {
+      if (v == 1) return pick_b_v<T, L, 1, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
+      if (v == 3) return pick_b_v<T, L, 3, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
+    }
   }
   return cudaErrorInvalidConfiguration;
 }
@@ -797,18 +815,19 @@ cudaError_t pick_b(int cb, int v, const void* Z, int n2, const void* twB, const 
 
 template <typename T>
 cudaError_t dispatch_a(int log2_n2, int ca, int v, const void* G, int64_t lc, int64_t n, int n1, const void* twA,
-                       const void* hi, const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st) {
+                       const void* hi, const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st,
+                       int res = 0) {
   switch (log2_n2) {
-    FSTAT_LEN_CASES(pick_a, >(ca, v, G, lc, n, n1, twA, hi, lo, h, coef, Z, st))
+    FSTAT_LEN_CASES(pick_a, >(ca, v, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res))
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename T, int MODE>
 cudaError_t dispatch_b(int log2_n1, int cb, int v, const void* Z, int n2, const void* twB, const SkyConst* sky,
-                       float* out, const PeakArgs& pk, cudaStream_t st) {
+                       float* out, const PeakArgs& pk, cudaStream_t st, int res = 0) {
   switch (log2_n1) {
-    FSTAT_LEN_CASES(pick_b, , MODE>(cb, v, Z, n2, twB, sky, out, pk, st))
+    FSTAT_LEN_CASES(pick_b, , MODE>(cb, v, Z, n2, twB, sky, out, pk, st, res))
     default: return cudaErrorInvalidValue;
   }
 }

@@ -67,7 +67,8 @@ struct fstat_plan {
   void* tw = nullptr;            // twiddle tables for the current split
   TwiddleTables tt{};
   int ca = 0, cb = 0;            // CTA shapes of pass A / pass B (0 = default)
-  int va = 0, vb = 0;            // radix schedules of pass A / pass B
+  int va = 0, vb = 0;            // schedules of pass A / pass B (bit 0 radix-8 first, bit 1 one buffer)
+  int ra = 0, rb = 0;            // persistent CTAs per SM of pass A / pass B (0 = all resident)
   int* d_err = nullptr;   // [0] sticky kernel error, [1] scratch for input checks
   int* h_err = nullptr;   // pinned
   fstat_template* d_tmpl = nullptr;
@@ -220,28 +221,31 @@ int set_split(fstat_plan* p, int log2n1) {
   return FSTAT_OK;
 }
 
-cudaError_t launch_a(fstat_plan* p, int ca, int va, const TmplCoef* coef, cudaStream_t st, void* Z = nullptr) {
+cudaError_t launch_a(fstat_plan* p, int ca, int va, const TmplCoef* coef, cudaStream_t st, void* Z = nullptr,
+                     int res = -1) {
   const TwiddleTables& t = p->tt;
   if (!Z) Z = p->Z;
+  if (res < 0) res = p->ra;
   return p->d.precision == FSTAT_FP64
-      ? launch_pass_a_f64(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, Z, st)
-      : launch_pass_a_f32(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, Z, st);
+      ? launch_pass_a_f64(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, Z, st, res)
+      : launch_pass_a_f32(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, Z, st, res);
 }
 
 cudaError_t launch_b(fstat_plan* p, int cb, int vb, float* out, cudaStream_t st, void* Z = nullptr,
-                     const PeakArgs* pk = nullptr) {
+                     const PeakArgs* pk = nullptr, int res = -1) {
   const TwiddleTables& t = p->tt;
   if (!Z) Z = p->Z;
+  if (res < 0) res = p->rb;
   return p->d.precision == FSTAT_FP64
-      ? launch_pass_b_f64(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk)
-      : launch_pass_b_f32(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk);
+      ? launch_pass_b_f64(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk, res)
+      : launch_pass_b_f32(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk, res);
 }
 
 cudaError_t launch_b_acc(fstat_plan* p, float* out, int shift, cudaStream_t st, void* Z) {
   const TwiddleTables& t = p->tt;
   return p->d.precision == FSTAT_FP64
-      ? launch_pass_b_acc_f64(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st)
-      : launch_pass_b_acc_f32(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st);
+      ? launch_pass_b_acc_f64(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st, p->rb)
+      : launch_pass_b_acc_f32(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st, p->rb);
 }
 
 }  // namespace
@@ -839,8 +843,22 @@ int fstat_get_cta(const fstat_plan* p, int* ca, int* va, int* cb, int* vb) {
   return FSTAT_OK;
 }
 
+int fstat_set_residency(fstat_plan* p, int ra, int rb) {
+  if (!p || ra < 0 || rb < 0 || ra > 32 || rb > 32) return FSTAT_ERR_INVALID_ARG;
+  p->ra = ra;
+  p->rb = rb;
+  return FSTAT_OK;
+}
+
+int fstat_get_residency(const fstat_plan* p, int* ra, int* rb) {
+  if (!p || !ra || !rb) return FSTAT_ERR_INVALID_ARG;
+  *ra = p->ra;
+  *rb = p->rb;
+  return FSTAT_OK;
+}
+
 int fstat_set_cta(fstat_plan* p, int ca, int va, int cb, int vb) {
-  if (!p || ca < 0 || cb < 0 || ca > 32 || cb > 32 || va < 0 || va > 1 || vb < 0 || vb > 1)
+  if (!p || ca < 0 || cb < 0 || ca > 32 || cb > 32 || va < 0 || va > 3 || vb < 0 || vb > 3)
     return FSTAT_ERR_INVALID_ARG;
   p->ca = ca;
   p->va = va;
@@ -968,7 +986,7 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
     launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, 0, kPipe, p->d_coef, st);
     // isolated timings of every compiled shape of each pass
     std::vector<std::pair<float, std::pair<int, int>>> ta, tb;
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < 4; ++v) {  // schedules: radix-8 first (bit 0), one buffer (bit 1)
       for (int c : kCa) {
         float ms = time_pass(p, 0, c, v, p->d_coef, out, st, e0, e1);
         if (ms > 0.f) ta.push_back({ms, {c, v}});

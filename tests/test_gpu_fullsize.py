@@ -46,7 +46,7 @@ def test_every_split_and_cta_shape(log2n, n):
             plan.set_data(X, x[X], t.sigmas[X])
         for l1 in range(max(5, log2n - 12), min(12, log2n - 5) + 1):
             plan.set_split(1 << l1)
-            for v in (0, 1):
+            for v in (0, 1, 2, 3):   # radix-8 first (bit 0), one shared buffer (bit 1)
                 for ca, cb in [(0, 0), (1, 1), (2, 2), (4, 4), (1, 8), (2, 8)]:
                     plan.set_cta(ca, cb, v, v)
                     try:

@@ -207,3 +207,26 @@ def test_physical_units_give_the_same_2F():
     got = run_gpu(t, xs, tm, sigmas=sig)
     assert np.all(np.isfinite(got))
     assert_parity(got, ref, rel=1e-4, abs_=1e-3)
+
+
+def test_residency_caps_and_single_buffer_schedules_give_identical_2F():
+    # The per-SM cap of the persistent passes and the one-buffer schedules
+    # change only how tiles are scheduled, never the arithmetic: bitwise.
+    t = small(seed=12, n_fft=1 << 18, n_samples=100_003, dt=1.0)
+    x = synth.make_data(t)
+    tm = t.templates()[:3]
+    with pkg.FstatPlan.from_target(t) as plan:
+        for X in range(2):
+            plan.set_data(X, x[X], t.sigmas[X])
+        plan.set_split(512)            # both passes of length 512: every schedule compiled
+        plan.set_cta(2, 2, 0, 0)
+        base = plan.compute(tm).cpu().numpy()
+        for ra, rb in ((1, 1), (2, 1), (1, 3)):
+            plan.set_residency(ra, rb)
+            assert np.array_equal(plan.compute(tm).cpu().numpy(), base)
+        plan.set_residency(0, 0)
+        plan.set_cta(2, 2, 2, 2)
+        assert np.array_equal(plan.compute(tm).cpu().numpy(), base)
+        with pytest.raises(pkg.FstatError):
+            plan.set_residency(-1, 0)
+    assert_parity(base, resamp.fstat(t, x, tm))
