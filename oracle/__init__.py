@@ -21,10 +21,11 @@ continuous gravitational wave searches", arXiv:2201.00451):
 * ``semicoh``   -- semi-coherent sum of per-segment 2F with nearest-bin
                    sliding (Sec. 6).
 * ``interp_study`` -- accuracy of the step-(v) interpolator variants.
+* ``sft``       -- step (ii): x_h from short Fourier transforms (Sec. 3).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA
 library and never imports it.
 """
 
-from . import geometry, resamp, demod, synth, metrics, grad, peaks, semicoh  # noqa: F401
+from . import geometry, resamp, demod, synth, metrics, grad, peaks, semicoh, sft  # noqa: F401
