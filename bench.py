@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-interp", action="store_true")
     ap.add_argument("--no-semicoh", action="store_true")
     ap.add_argument("--no-skyheavy", action="store_true")
+    ap.add_argument("--no-sft", action="store_true")
     ap.add_argument("--streams", type=int, default=2, help="template streams per plan (1..8)")
     ap.add_argument("--shape", default="", help="n1,ca,va,cb,vb: fixed FFT split and CTA shapes (skip autotune)")
     return ap.parse_args()
@@ -417,6 +418,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_skyheavy:
         line["sky_heavy"] = sky_heavy_bench(t, xs, dev, stream, args)
 
+    # step (ii): x_h from SFTs on the device, once per data set
+    if rank == 0 and not args.no_sft:
+        line["sft_to_xh"] = sft_bench(t, dev)
+
     # semi-coherent search: ten 10-day segments summed on the device
     if rank == 0 and not args.no_semicoh:
         line["semicoherent"] = semicoh_bench(dev, stream, args)
@@ -717,6 +722,37 @@ def sky_heavy_bench(t, xs, dev, stream, args, n_sky=128, n_f1=11):
             "per_sky_ms": ms_sky / max(n_sky_runs, 1),
             "workload": f"10-day H1+L1 data, {n_sky} sky positions x {n_f1} f1dot, FFT 2^22, "
                         "per-sky work for every position in every step"}
+
+
+def sft_bench(t, dev, reps=3):
+    """Step (ii) on the GPU for the 10-day two-detector data: 480 SFTs of
+    1800 s per detector, a 2 Hz band of 3600 bins around f_h (dt = 0.5 s,
+    1 728 000 samples), complex64 bins in pinned host memory (seeded complex
+    Gaussian, the statistics of SFT bins of white noise).  Times
+    fstat_set_sfts for both detectors: the host-to-device copy, the direct
+    inverse transforms and the finiteness check."""
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+
+    n_sft, nb, t_sft = 480, 3600, 1800.0
+    q0 = int(round(t.f_het * t_sft)) - nb // 2
+    bins = [torch.from_numpy(make_noise(t.seed + 31 * X, X, n_sft * nb, 1.0, "c64").reshape(n_sft, nb)).pin_memory()
+            for X in range(len(t.detectors))]
+    plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
+    for X in range(len(t.detectors)):
+        plan.set_sfts(X, bins[X].numpy(), q0, t_sft, 2 * nb, 1.0)
+    torch.cuda.synchronize(dev)
+    s = time.perf_counter()
+    for _ in range(reps):
+        for X in range(len(t.detectors)):
+            plan.set_sfts(X, bins[X].numpy(), q0, t_sft, 2 * nb, 1.0)
+    torch.cuda.synchronize(dev)
+    sec = (time.perf_counter() - s) / reps
+    plan.close()
+    return {"value": sec * 1e3, "unit": "ms per data set (2 detectors)",
+            "sft_bins_per_s": len(t.detectors) * n_sft * nb / sec,
+            "workload": f"{len(t.detectors)} det x {n_sft} SFTs of {t_sft:g} s, {nb}-bin band -> {n_sft * nb} samples"}
 
 
 def refine_bench(t, xs, dev, n_cand=4096, steps=20):

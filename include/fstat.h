@@ -125,6 +125,30 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out);
 int fstat_set_data(fstat_plan* plan, int det, const void* xh, int dtype, int64_t n,
                    double sigma, void* stream);
 
+/* Step (ii) of Sec. 3 on the GPU: detector `det`'s x_h from short Fourier
+ * transforms.  `bins` (HOST or DEVICE, n_sft x n_bins complex of `dtype`,
+ * row-major) holds, for each of n_sft consecutive SFTs of t_sft seconds
+ * (SFT s starts at t0 + s t_sft), the bins q0 .. q0 + n_bins - 1 of its DFT
+ * X_s[q] = sum_n x(t_s + n t_sft / m_raw) exp(-2 pi i q n / m_raw) over m_raw
+ * raw samples.  The band must be centred on f_het, which must lie on the
+ * SFT grid: q0 = f_het t_sft - n_bins / 2.  Per SFT the band is inverse
+ * transformed to n_bins samples,
+ *   x_h(t_s + m dt) = exp(-2 pi i f_het t_s) / m_raw * sum_i X_s[q0 + i] exp(2 pi i (i - n_bins/2) m / n_bins),
+ * so the plan's grid must be dt = t_sft / n_bins and n_samples = n_sft
+ * n_bins.  The series is stored in the plan's precision (complex64 for
+ * FSTAT_MIXED, complex128 for FSTAT_FP64); `sigma` is its per-quadrature
+ * noise level, as for fstat_set_data.  Synchronises `stream`.
+ * Errors: INVALID_ARG (grid or band mismatch, n_sft outside 1..65535),
+ * UNSUPPORTED (n_bins too large for the transform's shared memory: 12800
+ * for FSTAT_MIXED, 6400 for FSTAT_FP64), NONFINITE, OOM, CUDA. */
+int fstat_set_sfts(fstat_plan* plan, int det, const void* bins, int dtype, int64_t n_sft, int64_t n_bins,
+                   int64_t q0, double t_sft, int64_t m_raw, double sigma, void* stream);
+
+/* Copy detector `det`'s stored series (n_samples complex values) to `out`
+ * (host or device).  Returns its dtype (FSTAT_C64 or FSTAT_C128, >= 0) or a
+ * negative error (INVALID_ARG, NOT_READY).  Synchronises `stream`. */
+int fstat_export_data(fstat_plan* plan, int det, void* out, void* stream);
+
 /* 2F for n_tmpl templates.  `tmpl` is a HOST array of n_tmpl templates;
  * `twoF` is a caller-owned DEVICE buffer of n_tmpl * n_fft floats, written
  * row-major [template][bin] in ascending frequency.  Templates are grouped

@@ -46,6 +46,7 @@ EXPORTS = (
     "fstat_grad", "fstat_batch_create", "fstat_batch_add", "fstat_batch_instantiate",
     "fstat_batch_launch", "fstat_batch_nodes", "fstat_batch_destroy", "fstat_set_streams",
     "fstat_compute_peaks", "fstat_semicoherent", "fstat_set_residency", "fstat_get_residency",
+    "fstat_set_sfts", "fstat_export_data",
 )
 
 
@@ -141,6 +142,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fstat_compute_peaks": (i32, [P, P, i64, ctypes.POINTER(PeakOut), P]),
         "fstat_semicoherent": (i32, [ctypes.POINTER(P), i32, P, i64, dbl, P, P]),
         "fstat_set_residency": (i32, [P, i32, i32]),
+        "fstat_set_sfts": (i32, [P, i32, P, i32, i64, i64, i64, dbl, i64, dbl, P]),
+        "fstat_export_data": (i32, [P, i32, P, P]),
         "fstat_get_residency": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
@@ -265,6 +268,32 @@ class FstatPlan:
         rc = self._lib.fstat_set_data(self._p, int(det), ctypes.c_void_p(ptr), dtype, int(len(keep)),
                                       float(sigma), _stream_handle(stream))
         _check(rc, "fstat_set_data")
+
+    def set_sfts(self, det: int, bins, q0: int, t_sft: float, m_raw: int, sigma: float, stream=None):
+        """fstat_set_sfts: x_h of detector ``det`` from SFT band bins, a numpy
+        array (host) or CUDA tensor [n_sft, n_bins] of complex64/complex128."""
+        if isinstance(bins, np.ndarray):
+            b = np.ascontiguousarray(bins)
+            dtype = {np.dtype(np.complex64): C64, np.dtype(np.complex128): C128}[b.dtype]
+            ptr, shape = b.ctypes.data, b.shape
+        else:
+            import torch
+            b = bins.contiguous()
+            dtype = {torch.complex64: C64, torch.complex128: C128}[b.dtype]
+            ptr, shape = b.data_ptr(), tuple(b.shape)
+        rc = self._lib.fstat_set_sfts(self._p, int(det), ctypes.c_void_p(ptr), dtype, int(shape[0]), int(shape[1]),
+                                      int(q0), float(t_sft), int(m_raw), float(sigma), _stream_handle(stream))
+        _check(rc, "fstat_set_sfts")
+
+    def export_data(self, det: int, stream=None) -> np.ndarray:
+        """The stored series of detector ``det`` (complex64 or complex128)."""
+        out = np.empty(self.n_samples, dtype=np.complex128)
+        rc = self._lib.fstat_export_data(self._p, int(det), ctypes.c_void_p(out.ctypes.data), _stream_handle(stream))
+        if rc < 0:
+            _check(rc, "fstat_export_data")
+        if rc == C64:
+            return out.view(np.complex64)[: self.n_samples].copy()
+        return out
 
     def compute(self, templates, out=None, stream=None):
         """fstat_compute: returns a CUDA float32 tensor [n_templates, n_fft] of 2F

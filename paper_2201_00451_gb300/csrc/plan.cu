@@ -384,33 +384,39 @@ void fstat_plan_destroy(fstat_plan* p) {
   delete p;
 }
 
-int fstat_set_data(fstat_plan* p, int det, const void* xh, int dtype, int64_t n, double sigma,
-                   void* stream) {
-  if (!p || !xh || det < 0 || det >= p->d.n_det || n != p->d.n_samples || !(sigma > 0.0) ||
-      !std::isfinite(sigma) || (dtype != FSTAT_C64 && dtype != FSTAT_C128))
-    return FSTAT_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  size_t eb = dtype == FSTAT_C128 ? 16 : 8;
+}  // extern "C"
+
+namespace {
+
+// Device storage for detector `det`'s series in `dtype`; marks the series
+// (and everything derived from it) stale.
+int prepare_series(fstat_plan* p, int det, int dtype, cudaStream_t st) {
+  const size_t eb = dtype == FSTAT_C128 ? 16 : 8;
   if (p->xh[det] && p->dtype[det] != dtype) {
     CK(cudaStreamSynchronize(st));
     cudaFree(p->xh[det]);
     p->xh[det] = nullptr;
   }
-  if (!p->xh[det]) CK(cudaMalloc(&p->xh[det], (size_t)n * eb));
+  if (!p->xh[det]) CK(cudaMalloc(&p->xh[det], (size_t)p->d.n_samples * eb));
   p->dtype[det] = dtype;
   p->have[det] = false;
   p->sky_valid = false;
   p->gtab_valid = false;
-  CK(cudaMemcpyAsync(p->xh[det], xh, (size_t)n * eb, cudaMemcpyDefault, st));
+  return FSTAT_OK;
+}
+
+// Check the stored series for NaN/Inf (synchronises) and update the noise
+// weights: common rescaling by the smallest sigma among the detectors with
+// data.
+int finish_series(fstat_plan* p, int det, double sigma, cudaStream_t st) {
   CK(cudaMemsetAsync(p->d_err + 1, 0, sizeof(int), st));
-  launch_check_finite(p->xh[det], dtype, n, p->d_err + 1, st);
+  launch_check_finite(p->xh[det], p->dtype[det], p->d.n_samples, p->d_err + 1, st);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(p->h_err + 1, p->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (p->h_err[1] != 0) return p->h_err[1];
   p->sigma[det] = sigma;
   p->have[det] = true;
-  // common rescaling by the smallest sigma among the detectors with data
   double ref = 0.0;
   for (int X = 0; X < p->d.n_det; ++X)
     if (p->have[X] && (ref == 0.0 || p->sigma[X] < ref)) ref = p->sigma[X];
@@ -419,6 +425,67 @@ int fstat_set_data(fstat_plan* p, int det, const void* xh, int dtype, int64_t n,
   for (int X = 0; X < p->d.n_det; ++X)
     p->geo.w[X] = p->have[X] ? ref * ref / (2.0 * p->sigma[X] * p->sigma[X]) : 0.0;
   return FSTAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fstat_set_data(fstat_plan* p, int det, const void* xh, int dtype, int64_t n, double sigma,
+                   void* stream) {
+  if (!p || !xh || det < 0 || det >= p->d.n_det || n != p->d.n_samples || !(sigma > 0.0) ||
+      !std::isfinite(sigma) || (dtype != FSTAT_C64 && dtype != FSTAT_C128))
+    return FSTAT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = prepare_series(p, det, dtype, st);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(p->xh[det], xh, (size_t)n * (dtype == FSTAT_C128 ? 16 : 8), cudaMemcpyDefault, st));
+  return finish_series(p, det, sigma, st);
+}
+
+int fstat_set_sfts(fstat_plan* p, int det, const void* bins, int dtype, int64_t n_sft, int64_t n_bins,
+                   int64_t q0, double t_sft, int64_t m_raw, double sigma, void* stream) {
+  if (!p || !bins || det < 0 || det >= p->d.n_det || (dtype != FSTAT_C64 && dtype != FSTAT_C128) ||
+      n_sft < 1 || n_sft > 65535 || n_bins < 2 || n_bins > INT32_MAX || m_raw < n_bins ||
+      !(t_sft > 0.0) || !std::isfinite(t_sft) || !(sigma > 0.0) || !std::isfinite(sigma) ||
+      n_sft * n_bins != p->d.n_samples)
+    return FSTAT_ERR_INVALID_ARG;
+  // the output grid is the plan's: dt = t_sft / n_bins, starting at t0
+  if (std::fabs(t_sft / (double)n_bins - p->d.dt) > 1e-12 * p->d.dt) return FSTAT_ERR_INVALID_ARG;
+  // the band is the n_bins bins centred on f_het, which lies on the SFT grid
+  const double qh = p->d.f_het * t_sft;
+  if (std::fabs(qh - std::rint(qh)) > 1e-6 || (int64_t)std::rint(qh) - n_bins / 2 != q0)
+    return FSTAT_ERR_INVALID_ARG;
+  if (sft_smem_bytes((int)n_bins, p->d.precision) > (size_t)220 * 1024) return FSTAT_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int out_dtype = p->d.precision == FSTAT_FP64 ? FSTAT_C128 : FSTAT_C64;
+  int rc = prepare_series(p, det, out_dtype, st);
+  if (rc) return rc;
+  // the bins on the device (host input copied), and the roots of unity
+  const size_t in_bytes = (size_t)n_sft * n_bins * (dtype == FSTAT_C128 ? 16 : 8);
+  void* dbins = nullptr;
+  void* roots = nullptr;
+  cudaError_t e = cudaMalloc(&dbins, in_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&roots, (size_t)n_bins * 16);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dbins, bins, in_bytes, cudaMemcpyDefault, st);
+  if (e == cudaSuccess)
+    e = launch_sft_to_xh(p->d.precision, dtype, dbins, n_sft, (int)n_bins, p->d.f_het, p->d.t0, t_sft, m_raw,
+                         roots, p->xh[det], st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (dbins) cudaFree(dbins);
+  if (roots) cudaFree(roots);
+  if (e != cudaSuccess) return cuda_status(e);
+  return finish_series(p, det, sigma, st);
+}
+
+int fstat_export_data(fstat_plan* p, int det, void* out, void* stream) {
+  if (!p || !out || det < 0 || det >= p->d.n_det) return FSTAT_ERR_INVALID_ARG;
+  if (!p->have[det]) return FSTAT_ERR_NOT_READY;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t eb = p->dtype[det] == FSTAT_C128 ? 16 : 8;
+  CK(cudaMemcpyAsync(out, p->xh[det], (size_t)p->d.n_samples * eb, cudaMemcpyDefault, st));
+  CK(cudaStreamSynchronize(st));
+  return p->dtype[det];
 }
 
 }  // extern "C"
