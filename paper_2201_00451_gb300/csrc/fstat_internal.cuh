@@ -190,12 +190,6 @@ cudaError_t launch_pass_b_acc_f32(int log2_n1, int cb, int vb, const void* Z, in
                                   const SkyConst* sky, float* out, int shift, cudaStream_t st, int res = 0);
 cudaError_t launch_pass_b_acc_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                                   const SkyConst* sky, float* out, int shift, cudaStream_t st, int res = 0);
-// Step (ii) from SFTs (sft.cu): shared memory of the transform kernel and
-// its launch (roots: scratch of B 16-byte entries).
-size_t sft_smem_bytes(int B, int precision);
-cudaError_t launch_sft_to_xh(int precision, int in_dtype, const void* bins, int64_t n_sft, int B, double f_het,
-                             double t_start, double t_sft, int64_t m_raw, void* roots, void* xh,
-                             cudaStream_t st);
 // Band keys of n rows x n_bands -> maximum 2F and its bin (band_bin may be null).
 cudaError_t launch_band_decode(const unsigned long long* keys, int64_t count, float* band_max,
                                int32_t* band_bin, cudaStream_t st);

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "fstat_internal.cuh"
+#include "sft.cuh"
 
 using namespace fstat;
 

@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include "fstat_internal.cuh"
+#include "sft.cuh"
 
 namespace fstat {
 
