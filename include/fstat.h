@@ -196,6 +196,15 @@ typedef struct {
 int fstat_compute_peaks(fstat_plan* plan, const fstat_template* tmpl, int64_t n_tmpl,
                         const fstat_peak_out* out, void* stream);
 
+/* The same reduction applied to 2F rows already in DEVICE memory (for
+ * example the output of fstat_semicoherent): `twoF` holds n_rows rows of
+ * n_fft floats (16-byte aligned), bins in ascending frequency; row i is
+ * reported as template tmpl_offset + i.  Uses the plan's band-key scratch.
+ * Errors: INVALID_ARG (as fstat_compute_peaks, misaligned twoF),
+ * UNSUPPORTED (n_fft not a multiple of 4096), OOM, CUDA. */
+int fstat_reduce_peaks(fstat_plan* plan, const float* twoF, int64_t n_rows, const fstat_peak_out* out,
+                       void* stream);
+
 /* Semi-coherent sum over segments (Sec. 6: the data are split into segments
  * of about ten days, each searched with the F-statistic, and the segments'
  * 2F summed, all on the GPU).  seg[0..n_seg) are plans over consecutive

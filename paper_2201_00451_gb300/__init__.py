@@ -46,7 +46,7 @@ EXPORTS = (
     "fstat_grad", "fstat_batch_create", "fstat_batch_add", "fstat_batch_instantiate",
     "fstat_batch_launch", "fstat_batch_nodes", "fstat_batch_destroy", "fstat_set_streams",
     "fstat_compute_peaks", "fstat_semicoherent", "fstat_set_residency", "fstat_get_residency",
-    "fstat_set_sfts", "fstat_export_data",
+    "fstat_set_sfts", "fstat_export_data", "fstat_reduce_peaks",
 )
 
 
@@ -144,6 +144,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fstat_set_residency": (i32, [P, i32, i32]),
         "fstat_set_sfts": (i32, [P, i32, P, i32, i64, i64, i64, dbl, i64, dbl, P]),
         "fstat_export_data": (i32, [P, i32, P, P]),
+        "fstat_reduce_peaks": (i32, [P, P, i64, ctypes.POINTER(PeakOut), P]),
         "fstat_get_residency": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
@@ -316,6 +317,13 @@ class FstatPlan:
                                      ctypes.c_void_p(out_ptr), _stream_handle(stream))
         _check(rc, "fstat_compute")
 
+    def reduce_peaks(self, twoF, threshold: float = 70.0, n_bands: int = 0, capacity: int = 4096,
+                     tmpl_offset: int = 0, out=None, stream=None):
+        """fstat_reduce_peaks: the peaks reduction of a CUDA float32 tensor
+        [n_rows, n_fft] of 2F already on the device; same result dict as
+        compute_peaks."""
+        return self._peaks(None, twoF, threshold, n_bands, capacity, tmpl_offset, out, stream)
+
     def compute_peaks(self, templates, threshold: float = 70.0, n_bands: int = 0, capacity: int = 4096,
                       tmpl_offset: int = 0, out=None, stream=None):
         """fstat_compute_peaks: 2F reduced on the device.  Returns a dict of
@@ -325,9 +333,18 @@ class FstatPlan:
         ``band_max`` (float32 [n, n_bands]) and ``band_bin`` (int32).
         ``out`` may pass such a dict back in to append to its list (its band
         buffers are reused when their shape fits)."""
+        return self._peaks(templates, None, threshold, n_bands, capacity, tmpl_offset, out, stream)
+
+    def _peaks(self, templates, twoF, threshold, n_bands, capacity, tmpl_offset, out, stream):
         import torch
-        t = as_templates(templates)
-        n = len(t)
+        if templates is not None:
+            t = as_templates(templates)
+            n = len(t)
+        else:
+            if twoF.dtype != torch.float32 or not twoF.is_cuda or not twoF.is_contiguous() or \
+                    twoF.dim() != 2 or twoF.shape[1] != self.n_fft:
+                raise ValueError("twoF must be a contiguous CUDA float32 tensor [n_rows, n_fft]")
+            n = twoF.shape[0]
         if out is None:
             out = {"count": torch.zeros(1, dtype=torch.int64, device="cuda"),
                    "peaks": torch.empty((max(capacity, 0), 4), dtype=torch.int32, device="cuda")}
@@ -346,9 +363,14 @@ class FstatPlan:
         po.n_peaks = out["count"].data_ptr() if out.get("count") is not None else None
         po.band_max = out["band_max"].data_ptr() if n_bands > 0 else None
         po.band_bin = out["band_bin"].data_ptr() if n_bands > 0 else None
-        rc = self._lib.fstat_compute_peaks(self._p, ctypes.c_void_p(t.ctypes.data), n, ctypes.byref(po),
-                                           _stream_handle(stream))
-        _check(rc, "fstat_compute_peaks")
+        if templates is not None:
+            rc = self._lib.fstat_compute_peaks(self._p, ctypes.c_void_p(t.ctypes.data), n, ctypes.byref(po),
+                                               _stream_handle(stream))
+            _check(rc, "fstat_compute_peaks")
+        else:
+            rc = self._lib.fstat_reduce_peaks(self._p, ctypes.c_void_p(twoF.data_ptr()), n, ctypes.byref(po),
+                                              _stream_handle(stream))
+            _check(rc, "fstat_reduce_peaks")
         return out
 
     def grad(self, candidates, stream=None):

@@ -40,6 +40,12 @@ struct TmplCoef {
   int pad_;
 };
 
+// One entry of the sky-independent timing table (sky.cu): cos, sin of the
+// orbital phase and of the sidereal rotation angle.
+struct alignas(32) TimeTab {
+  double co, so, cq, sq;
+};
+
 // Geometry constants for one plan (kernel argument, by value).
 struct Geo {
   double c, au, r_earth, w_rot, w_orb, cos_obl, sin_obl, orb_ph0, sid_ph0;
@@ -54,7 +60,7 @@ struct Geo {
   double clon[kMaxDet], slon[kMaxDet]; // cos, sin of the longitudes
   // Sky-independent timing table (sky.cu): cos, sin of the orbital phase and
   // of the sidereal rotation angle at t = tab_t0 + i / tab_inv_h.
-  const double4* tab;
+  const TimeTab* tab;
   double tab_t0, tab_inv_h;
   int tab_n;
   // Roemer delay t_m of the current sky position for each detector on the
@@ -117,7 +123,7 @@ void launch_sky(const Geo& g, int precision, double alpha, double delta, const v
 // Timing table: entries needed to cover [t_lo, t_hi] at spacing h, and the
 // kernel that fills them (FP64 sincos, once per plan).
 int time_table_entries(double t_lo, double t_hi, double h);
-cudaError_t launch_time_table(const Geo& g, double4* tab, cudaStream_t st);
+cudaError_t launch_time_table(const Geo& g, TimeTab* tab, cudaStream_t st);
 void launch_tmpl_coef(const SkyConst* sky, double dt, const fstat_template* tmpl,
                       const int* order, int first, int count, TmplCoef* out, cudaStream_t st);
 void launch_check_finite(const void* x, int dtype, int64_t n, int* err, cudaStream_t st);

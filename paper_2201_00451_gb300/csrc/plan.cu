@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "fstat_internal.cuh"
+#include "reduce_peaks.cuh"
 #include "sft.cuh"
 
 using namespace fstat;
@@ -62,7 +63,7 @@ struct fstat_plan {
   cudaEvent_t join[kMaxStreams] = {};
   double* partials = nullptr;
   int nblk = 0;
-  double4* tab = nullptr;        // timing table (geo.tab)
+  TimeTab* tab = nullptr;        // timing table (geo.tab)
   double* tm_tab = nullptr;      // per-sky Roemer delay table (geo.tm_tab)
   SkyConst* sky = nullptr;
   void* tw = nullptr;            // twiddle tables for the current split
@@ -346,8 +347,8 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
     g.tab_n = time_table_entries(lo, hi, kTabStep);
     g.tab_t0 = lo;
     g.tab_inv_h = 1.0 / kTabStep;
-    double4* tab = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&tab, (size_t)g.tab_n * sizeof(double4));
+    TimeTab* tab = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&tab, (size_t)g.tab_n * sizeof(TimeTab));
     p->tab = tab;
     g.tab = tab;
     if (e == cudaSuccess) e = cudaMalloc(&p->tm_tab, (size_t)g.tab_n * kMaxDet * sizeof(double));
@@ -700,9 +701,12 @@ int fstat_semicoherent(fstat_plan* const* seg, int n_seg, const fstat_template* 
   return FSTAT_OK;
 }
 
-int fstat_compute_peaks(fstat_plan* p, const fstat_template* tmpl, int64_t n_tmpl, const fstat_peak_out* po,
-                        void* stream) {
-  if (!p || !po) return FSTAT_ERR_INVALID_ARG;
+namespace {
+
+// Checks of a peaks request shared by fstat_compute_peaks and
+// fstat_reduce_peaks, and the band-key scratch for n_rows rows.
+int peaks_request(fstat_plan* p, const fstat_peak_out* po, int64_t n_rows, int64_t* nkeys) {
+  if (!po) return FSTAT_ERR_INVALID_ARG;
   const bool list = po->n_peaks != nullptr;
   const bool bands = po->n_bands != 0;
   if (!list && !bands) return FSTAT_ERR_INVALID_ARG;
@@ -710,21 +714,55 @@ int fstat_compute_peaks(fstat_plan* p, const fstat_template* tmpl, int64_t n_tmp
     return FSTAT_ERR_INVALID_ARG;
   if (bands && (po->n_bands < 0 || po->n_bands > p->d.n_fft || ilog2_exact(po->n_bands) < 0 || !po->band_max))
     return FSTAT_ERR_INVALID_ARG;
+  *nkeys = bands ? n_rows * (int64_t)po->n_bands : 0;
+  if (*nkeys > p->keys_cap) {
+    CK(cudaDeviceSynchronize());
+    if (p->keys) cudaFree(p->keys);
+    p->keys = nullptr;
+    p->keys_cap = 0;
+    CK(cudaMalloc(&p->keys, (size_t)*nkeys * sizeof(unsigned long long)));
+    p->keys_cap = *nkeys;
+  }
+  return FSTAT_OK;
+}
+
+}  // namespace
+
+int fstat_reduce_peaks(fstat_plan* p, const float* twoF, int64_t n_rows, const fstat_peak_out* po,
+                       void* stream) {
+  if (!p || n_rows < 0 || (n_rows > 0 && !twoF) || ((uintptr_t)twoF & 15)) return FSTAT_ERR_INVALID_ARG;
+  if (p->d.n_fft % 4096) return FSTAT_ERR_UNSUPPORTED;
+  int64_t nkeys = 0;
+  int rc = peaks_request(p, po, n_rows, &nkeys);
+  if (rc || n_rows == 0) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (nkeys) CK(cudaMemsetAsync(p->keys, 0, (size_t)nkeys * sizeof(unsigned long long), st));
+  PeakArgs pk{};
+  pk.band_key = nkeys ? p->keys : nullptr;
+  pk.peaks = po->peaks;
+  pk.count = po->n_peaks;
+  pk.cap = po->n_peaks ? po->capacity : 0;
+  pk.tmpl = po->tmpl_offset;
+  pk.thr = po->threshold;
+  pk.log2_band = po->n_bands > 0 ? ilog2_exact(p->d.n_fft / po->n_bands) : 0;
+  CK(launch_reduce_peaks(twoF, n_rows, p->d.n_fft, pk, po->n_bands, st));
+  if (nkeys) CK(launch_band_decode(p->keys, nkeys, po->band_max, po->band_bin, st));
+  CK(cudaEventRecord(p->done, st));
+  return FSTAT_OK;
+}
+
+int fstat_compute_peaks(fstat_plan* p, const fstat_template* tmpl, int64_t n_tmpl, const fstat_peak_out* po,
+                        void* stream) {
+  if (!p || !po) return FSTAT_ERR_INVALID_ARG;
   int rc = validate_templates(p, tmpl, n_tmpl);
+  if (rc) return rc;
+  int64_t nkeys = 0;
+  rc = peaks_request(p, po, n_tmpl, &nkeys);
   if (rc) return rc;
   if (n_tmpl == 0) return FSTAT_OK;
   cudaStream_t st = (cudaStream_t)stream;
   rc = ensure_capacity(p, n_tmpl);
   if (rc) return rc;
-  const int64_t nkeys = bands ? n_tmpl * (int64_t)po->n_bands : 0;
-  if (nkeys > p->keys_cap) {
-    CK(cudaDeviceSynchronize());
-    if (p->keys) cudaFree(p->keys);
-    p->keys = nullptr;
-    p->keys_cap = 0;
-    CK(cudaMalloc(&p->keys, (size_t)nkeys * sizeof(unsigned long long)));
-    p->keys_cap = nkeys;
-  }
   if (p->staged_pending) { CK(cudaEventSynchronize(p->staged)); p->staged_pending = false; }
   std::memcpy(p->h_tmpl, tmpl, (size_t)n_tmpl * sizeof(fstat_template));
   sky_order(tmpl, n_tmpl, p->h_order);

@@ -72,19 +72,19 @@ __device__ __forceinline__ double tm_eval_d(const Geo& g, int X, double t, doubl
 // cos, sin of detector X's sidereal angle lon + rotation angle at t
 __device__ __forceinline__ Rot rot_eval(const Geo& g, int X, double t) {
   const TabPos p = tab_pos(g, t);
-  const double4 a = g.tab[p.i], b = g.tab[p.i + 1], c = g.tab[p.i + 2], d = g.tab[p.i + 3];
-  const double cq = p.w0 * a.z + p.w1 * b.z + p.w2 * c.z + p.w3 * d.z;
-  const double sq = p.w0 * a.w + p.w1 * b.w + p.w2 * c.w + p.w3 * d.w;
+  const TimeTab a = g.tab[p.i], b = g.tab[p.i + 1], c = g.tab[p.i + 2], d = g.tab[p.i + 3];
+  const double cq = p.w0 * a.cq + p.w1 * b.cq + p.w2 * c.cq + p.w3 * d.cq;
+  const double sq = p.w0 * a.sq + p.w1 * b.sq + p.w2 * c.sq + p.w3 * d.sq;
   return Rot{g.clon[X] * cq - g.slon[X] * sq, g.slon[X] * cq + g.clon[X] * sq};
 }
 
-__global__ void k_time_table(Geo g, double4* __restrict__ tab) {
+__global__ void k_time_table(Geo g, TimeTab* __restrict__ tab) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.tab_n; i += gridDim.x * blockDim.x) {
     const double t = g.tab_t0 + (double)i / g.tab_inv_h;
     double so, co, sq, cq;
     sincos(g.orb_ph0 + g.w_orb * t, &so, &co);
     sincos(g.sid_ph0 + g.w_rot * t, &sq, &cq);
-    tab[i] = make_double4(co, so, cq, sq);
+    tab[i] = TimeTab{co, so, cq, sq};
   }
 }
 
@@ -93,11 +93,11 @@ __global__ void k_sky_table(Geo g, const SkyConst* __restrict__ skyp) {
   const SkyConst& s = *skyp;
   const double py = g.cos_obl * s.ny + g.sin_obl * s.nz;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.tab_n; i += gridDim.x * blockDim.x) {
-    const double4 e = g.tab[i];
-    const double orb = g.au * (e.x * s.nx + e.y * py);
+    const TimeTab e = g.tab[i];
+    const double orb = g.au * (e.co * s.nx + e.so * py);
     for (int X = 0; X < g.n_det; ++X) {
-      const double cp = g.clon[X] * e.z - g.slon[X] * e.w;
-      const double sp = g.slon[X] * e.z + g.clon[X] * e.w;
+      const double cp = g.clon[X] * e.cq - g.slon[X] * e.sq;
+      const double sp = g.slon[X] * e.cq + g.clon[X] * e.sq;
       const double rot = g.rcl[X] * (cp * s.nx + sp * s.ny) + g.rsl[X] * s.nz;
       g.tm_tab[(int64_t)X * g.tab_n + i] = (orb + rot) / g.c;
     }
@@ -164,9 +164,7 @@ __global__ void k_sky_setup(Geo g, double alpha, double delta, SkyConst* out) {
 // value stays O(1) whatever the units of x_h (strain-scaled data would
 // overflow 1/(2 sigma^2) and |Fa|^2 in FP32).
 template <typename TIn, typename TZ>
-__global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* __restrict__ z,
-                                 const SkyConst* __restrict__ skyp) {
-  const SkyConst& s = *skyp;
+__global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* __restrict__ z) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < g.n;
        k += (int64_t)gridDim.x * blockDim.x) {
     double t = g.t0 + (double)k * g.dt;
@@ -355,11 +353,12 @@ __global__ void k_tmpl_coef(const SkyConst* __restrict__ sky, double dt,
   out[first + i] = c;
 }
 
+// (after k_sky_table on the same stream: the phase uses this sky's t_m)
 template <typename TIn, typename TZ>
-void launch_phase(const Geo& g, int X, const void* xh, void* z, const SkyConst* sky, cudaStream_t st) {
+void launch_phase(const Geo& g, int X, const void* xh, void* z, cudaStream_t st) {
   int blocks = (int)((g.n + 255) / 256);
   if (blocks > 152 * 64) blocks = 152 * 64;
-  k_detector_phase<TIn, TZ><<<blocks, 256, 0, st>>>(g, X, (const TIn*)xh, (TZ*)z + (int64_t)X * g.n, sky);
+  k_detector_phase<TIn, TZ><<<blocks, 256, 0, st>>>(g, X, (const TIn*)xh, (TZ*)z + (int64_t)X * g.n);
 }
 
 }  // namespace
@@ -368,7 +367,7 @@ int time_table_entries(double t_lo, double t_hi, double h) {
   return (int)std::ceil((t_hi - t_lo) / h) + 1;
 }
 
-cudaError_t launch_time_table(const Geo& g, double4* tab, cudaStream_t st) {
+cudaError_t launch_time_table(const Geo& g, TimeTab* tab, cudaStream_t st) {
   const int blocks = (g.tab_n + 255) / 256;
   k_time_table<<<blocks, 256, 0, st>>>(g, tab);
   return cudaGetLastError();
@@ -382,11 +381,11 @@ void launch_sky(const Geo& g, int precision, double alpha, double delta, const v
   for (int X = 0; X < g.n_det; ++X) {
     bool in64 = xh_dtype[X] == FSTAT_C128;
     if (precision == FSTAT_FP64) {
-      if (in64) launch_phase<double2, double2>(g, X, xh[X], z, sky, st);
-      else launch_phase<float2, double2>(g, X, xh[X], z, sky, st);
+      if (in64) launch_phase<double2, double2>(g, X, xh[X], z, st);
+      else launch_phase<float2, double2>(g, X, xh[X], z, st);
     } else {
-      if (in64) launch_phase<double2, float2>(g, X, xh[X], z, sky, st);
-      else launch_phase<float2, float2>(g, X, xh[X], z, sky, st);
+      if (in64) launch_phase<double2, float2>(g, X, xh[X], z, st);
+      else launch_phase<float2, float2>(g, X, xh[X], z, st);
     }
   }
   if (precision == FSTAT_FP64) {

@@ -157,3 +157,48 @@ def test_full_size_120_day_search_slice():
         v = got[k, inj.bin_index]
         sd = np.sqrt(2.0 * (4.0 + 2.0 * inj.rho2))
         assert abs(v - (4.0 + inj.rho2)) < 5.0 * sd + 0.02 * inj.rho2, (inj.rho2, v)
+
+
+def test_full_size_peaks_and_semicoherent_agree_with_dense_passes():
+    # 2^22 bins, the shapes the autotuner picks: compute_peaks against the
+    # dense output reduced in numpy (bitwise), and fstat_semicoherent over two
+    # 10-day segments against the dense per-segment rows shifted and added
+    # in float32 in segment order (bitwise)
+    import dataclasses
+
+    from oracle import semicoh
+    from workloads import make_noise
+
+    t = config2()
+    tm = t.templates()[::4096][:3]
+    plans = []
+    for k in range(2):
+        seg = dataclasses.replace(t, t0=t.t0 + k * t.n_samples * t.dt, injections=(), name=f"seg{k}")
+        p = pkg.FstatPlan.from_target(seg)
+        for X in range(2):
+            p.set_data(X, make_noise(t.seed + 13 * k, X, t.n_samples, t.sigmas[X], "c64"), t.sigmas[X])
+        p.autotune()
+        plans.append(p)
+    dense = [p.compute(tm).cpu().numpy() for p in plans]
+    out = plans[0].compute_peaks(tm, threshold=20.0, n_bands=1024, capacity=1 << 16)
+    plans[0].sync()
+    blocks = dense[0].reshape(len(tm), 1024, -1)
+    assert np.array_equal(out["band_max"].cpu().numpy(), blocks.max(axis=2))
+    assert int(out["count"].item()) == int((dense[0] > 20.0).sum())
+    t_ref = t.t0 + (2 * t.n_samples // 2) * t.dt
+    total = pkg.semicoherent(plans, tm, t_ref).cpu().numpy()
+    df = 1.0 / (t.n_fft * t.dt)
+    want = np.zeros_like(total)
+    for k, p in enumerate(plans):
+        seg_t_ref = t.t0 + k * t.n_samples * t.dt + (t.n_samples // 2) * t.dt
+        d_ref = seg_t_ref - t_ref
+        seg_tm = semicoh.segment_template(tm, d_ref)
+        rows = p.compute(seg_tm).cpu().numpy()
+        for i in range(len(tm)):
+            sh = semicoh.segment_shift(df, d_ref, float(tm["f1dot"][i]), float(tm["f2dot"][i]))
+            m = np.arange(t.n_fft)
+            ok = (m + sh >= 0) & (m + sh < t.n_fft)
+            want[i, ok] = want[i, ok] + rows[i, (m + sh)[ok]]
+    assert np.array_equal(total, want)
+    for p in plans:
+        p.close()

@@ -180,3 +180,64 @@ def test_full_size_band_maxima_and_injections():
     for i, inj in enumerate(t.injections[:2]):
         if ref[i, inj.bin_index] > 80.0:
             assert (i, inj.bin_index) in {(int(r["tmpl"]), int(r["bin"])) for r in lst}
+
+
+def test_reduce_peaks_of_dense_rows_equals_compute_peaks():
+    t, x, plan = setup(56, n_fft=1 << 16, n=40000)
+    tm = t.templates()
+    dense = plan.compute(tm)
+    for n_bands in (1, 256, 1 << 13):
+        a = plan.compute_peaks(tm, threshold=10.0, n_bands=n_bands, capacity=1 << 17)
+        b = plan.reduce_peaks(dense, threshold=10.0, n_bands=n_bands, capacity=1 << 17)
+        plan.sync()
+        assert torch.equal(a["band_max"], b["band_max"]) and torch.equal(a["band_bin"], b["band_bin"])
+        assert int(a["count"].item()) == int(b["count"].item())
+        la, lb = pkg.peaks_to_numpy(a), pkg.peaks_to_numpy(b)
+        assert sorted(zip(la["tmpl"].tolist(), la["bin"].tolist(), la["twoF"].tolist())) == \
+            sorted(zip(lb["tmpl"].tolist(), lb["bin"].tolist(), lb["twoF"].tolist()))
+    plan.close()
+
+
+def test_reduce_peaks_of_a_semicoherent_sum_matches_oracle():
+    from oracle import semicoh
+    from workloads import segment_slices, split_segments
+
+    S = 3
+    t = small_target(n_samples=S * 6000, dt=1.0, n_fft=1 << 14, n_det=2, n_inj=1, rho2_range=(300.0, 300.0),
+                     seed=57, f1dots=(0.0, -1e-10), f2dots=(0.0,), dtype="c64")
+    x = synth.make_data(t)
+    segs = split_segments(t, S)
+    data = [[xx[a:a + n] for xx in x] for a, n in segment_slices(t, S)]
+    plans = []
+    for s_, d in zip(segs, data):
+        p = pkg.FstatPlan.from_target(s_)
+        for X in range(2):
+            p.set_data(X, d[X], t.sigmas[X])
+        plans.append(p)
+    tm = t.templates()
+    total = pkg.semicoherent(plans, tm, t.t_reference)
+    out = plans[0].reduce_peaks(total, threshold=40.0, n_bands=64, capacity=1 << 16, tmpl_offset=5)
+    plans[0].sync()
+    ref = semicoh.semicoherent(segs, data, tm, t.t_reference)
+    check_bands(out["band_max"].cpu().numpy(), out["band_bin"].cpu().numpy(), ref, 64, abs_=ABS * S)
+    check_list(pkg.peaks_to_numpy(out), ref, 40.0, offset=5, abs_=ABS * S)
+    for p in plans:
+        p.close()
+
+
+def test_reduce_peaks_argument_checks():
+    t, x, plan = setup(58, n_fft=1 << 15)
+    rows = plan.compute(t.templates()[:2])
+    with pytest.raises(ValueError):
+        plan.reduce_peaks(rows[:, :100], n_bands=4)
+    with pytest.raises(pkg.FstatError) as e:
+        plan.reduce_peaks(rows, n_bands=3)
+    assert e.value.code == -1
+    plan.close()
+    t = small_target(n_samples=1000, dt=1.0, n_fft=1 << 10, n_det=1, seed=59, dtype="c64")
+    with pkg.FstatPlan.from_target(t) as small_plan:
+        small_plan.set_data(0, synth.make_data(t)[0], t.sigmas[0])
+        r = small_plan.compute(t.templates())
+        with pytest.raises(pkg.FstatError) as e:
+            small_plan.reduce_peaks(r, n_bands=1)
+        assert e.value.code == -7
