@@ -349,7 +349,9 @@ def run_ours(args, rank, world, local_rank):
     ms = reduce_max(ms, world, dev)
     total_tmpl = n_tmpl * args.steps * world
     value = total_tmpl / (ms / 1e3)
-    launches = args.steps * (len(chunks) + 2 * n_tmpl + 3 + len(t.detectors))
+    # per step: the per-sky kernels (setup, delay table, step iii per detector,
+    # resampling, finalize), one coefficient kernel per chunk, two passes per template
+    launches = args.steps * (len(chunks) + 2 * n_tmpl + 4 + len(t.detectors))
 
     # dominant kernel roofline (algorithmic bytes: 16 B per sample read for
     # pass A, 4 B per bin written for pass B)

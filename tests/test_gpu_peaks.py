@@ -241,3 +241,17 @@ def test_reduce_peaks_argument_checks():
         with pytest.raises(pkg.FstatError) as e:
             small_plan.reduce_peaks(r, n_bands=1)
         assert e.value.code == -7
+
+
+def test_empty_calls_return_without_work():
+    t, x, plan = setup(60, n_fft=1 << 14, n=8000)
+    empty = t.templates()[:0]
+    out = plan.compute_peaks(empty, threshold=10.0, n_bands=4)
+    plan.sync()
+    assert int(out["count"].item()) == 0 and out["band_max"].shape == (0, 4)
+    rows = torch.empty((0, t.n_fft), dtype=torch.float32, device="cuda")
+    out = plan.reduce_peaks(rows, threshold=10.0, n_bands=4)
+    plan.sync()
+    assert int(out["count"].item()) == 0
+    assert pkg.semicoherent([plan], empty, t.t_reference).shape == (0, t.n_fft)
+    plan.close()
