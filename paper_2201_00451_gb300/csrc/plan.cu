@@ -712,7 +712,8 @@ int peaks_request(fstat_plan* p, const fstat_peak_out* po, int64_t n_rows, int64
   if (!list && !bands) return FSTAT_ERR_INVALID_ARG;
   if (list && (std::isnan(po->threshold) || po->capacity < 0 || (po->capacity > 0 && !po->peaks)))
     return FSTAT_ERR_INVALID_ARG;
-  if (bands && (po->n_bands < 0 || po->n_bands > p->d.n_fft || ilog2_exact(po->n_bands) < 0 || !po->band_max))
+  if (bands && (po->n_bands < 0 || po->n_bands > p->d.n_fft || ilog2_exact(po->n_bands) < 0 ||
+                (n_rows > 0 && !po->band_max)))
     return FSTAT_ERR_INVALID_ARG;
   *nkeys = bands ? n_rows * (int64_t)po->n_bands : 0;
   if (*nkeys > p->keys_cap) {
