@@ -20,8 +20,8 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Work is enqueued asynchronously on it unless stated.
  *  - Errors found inside kernels (degenerate antenna matrix, non-finite
- *    input) are recorded in the plan and returned by fstat_sync() and by
- *    the next call that synchronises.
+ *    input, a bounded wait that ran out) are recorded in the plan and
+ *    returned by fstat_sync() and by the next call that synchronises.
  *  - A plan is not thread-safe; distinct plans may be used concurrently.
  *  - Times are seconds, angles radians, frequencies Hz.
  */
@@ -44,7 +44,8 @@ enum {
   FSTAT_ERR_DEGENERATE = -4,  /* D = AB - C^2 <= 1e-12 AB for a sky position  */
   FSTAT_ERR_NONFINITE = -5,   /* NaN or Inf in the input series               */
   FSTAT_ERR_NOT_READY = -6,   /* compute before every detector has data       */
-  FSTAT_ERR_UNSUPPORTED = -7  /* size outside the compiled FFT range          */
+  FSTAT_ERR_UNSUPPORTED = -7, /* size outside the compiled FFT range          */
+  FSTAT_ERR_TIMEOUT = -8      /* a kernel's bounded wait for its own copies ran out */
 };
 
 enum { FSTAT_MIXED = 0, /* FP64 timing/phases, FP32 resample/FFT/2F        */
@@ -272,7 +273,11 @@ int fstat_set_split(fstat_plan* plan, int64_t n1);
  * rows per CTA of pass B (cb), 0 = default for the length; schedule va /
  * vb: bit 0 = radix-8 first (lengths >= 1024, else radix-16 first), bit 1 =
  * one shared-memory buffer instead of two (no prefetch, half the shared
- * memory).  A shape that is not compiled for the current split makes
+ * memory); vb only: bit 2 = pass B tile loads by the tensor-memory-access
+ * engine (FP32, rows of 1024 points or more; a load that does not complete
+ * within a bounded wait ends the kernel, and fstat_sync() then returns
+ * FSTAT_ERR_TIMEOUT).  va 0..3,
+ * vb 0..7.  A shape that is not compiled for the current split makes
  * fstat_compute return FSTAT_ERR_CUDA.  fstat_get_cta reports the shapes
  * in effect (a default as its value for the current split). */
 int fstat_get_cta(const fstat_plan* plan, int* ca, int* va, int* cb, int* vb);

@@ -32,6 +32,7 @@ ERR = {
     -5: "FSTAT_ERR_NONFINITE",
     -6: "FSTAT_ERR_NOT_READY",
     -7: "FSTAT_ERR_UNSUPPORTED",
+    -8: "FSTAT_ERR_TIMEOUT",
 }
 MIXED, FP64 = 0, 1
 C64, C128 = 0, 1
@@ -447,7 +448,7 @@ class FstatPlan:
         _check(self._lib.fstat_set_cta(self._p, int(ca), int(va), int(cb), int(vb)), "fstat_set_cta")
 
     def set_streams(self, n: int):
-        """fstat_set_streams: templates rotate over n streams (1..4)."""
+        """fstat_set_streams: templates rotate over n streams (1..8)."""
         _check(self._lib.fstat_set_streams(self._p, int(n)), "fstat_set_streams")
 
     def autotune(self, stream=None):

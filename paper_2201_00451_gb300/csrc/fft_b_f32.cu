@@ -5,9 +5,15 @@ namespace fstat {
 
 cudaError_t launch_pass_b_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                               const SkyConst* sky, float* out, cudaStream_t st, const PeakArgs* pk,
-                              int res) {
-  if (pk) return launch_pass_b_peak_f32(log2_n1, cb, vb, Z, n2, twB, sky, *pk, st, res);
-  return fft::dispatch_b<float, fft::kStore>(log2_n1, cb, vb, Z, n2, twB, sky, out, PeakArgs{}, st, res);
+                              int res, int* err) {
+  if (pk) {
+    PeakArgs a = *pk;
+    if (!a.err) a.err = err;
+    return launch_pass_b_peak_f32(log2_n1, cb, vb, Z, n2, twB, sky, a, st, res);
+  }
+  PeakArgs a{};
+  a.err = err;
+  return fft::dispatch_b<float, fft::kStore>(log2_n1, cb, vb, Z, n2, twB, sky, out, a, st, res);
 }
 
 }  // namespace fstat

@@ -21,6 +21,10 @@
 // chosen per FFT length by the autotuner.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
+#include <stdint.h>
+#include <string.h> (the tensor map is encoded through the runtime's driver entry point)
+
 #include "fstat_internal.cuh"
 
 namespace fstat {
@@ -55,7 +59,8 @@ template <> struct TwT<double> { using type = double2; };
 // Schedule code V: bit 0 (lengths >= 1024) = radix-8 first (8 points per
 // thread, half the registers, one more pass); bit 1 = one shared buffer
 // (no prefetch), half the shared memory, so that a CTA of each pass fits
-// on one SM.  The first radix is the largest.
+// on one SM; bit 2 (pass B) = tiles loaded by bulk tensor copies (TMA)
+// instead of per-thread 16-byte copies.  The first radix is the largest.
 __host__ __device__ constexpr bool r8(int L, int V) { return (V & 1) && L >= 1024; }
 __host__ __device__ constexpr int np_of(int L, int V) { return r8(L, V) ? 4 : (L <= 256 ? 2 : 3); }
 __host__ __device__ constexpr int r_of(int L, int p, int V) {
@@ -131,6 +136,52 @@ template <typename PM> __device__ __forceinline__ void cp_pair(PM* dst, const PM
   cp_async16(dst, src);
   if constexpr (sizeof(PM) == 32) cp_async16((char*)dst + 16, (const char*)src + 16);
 }
+
+// Bulk tensor copies (TMA) for pass B's tiles: one thread issues a few 2D
+// box copies of the intermediate into shared memory, completion is counted
+// in bytes on an mbarrier, and every thread waits on the barrier's phase.
+// Each wait gives up after kWaitLimit polls (a GPU that stopped delivering
+// copies must not hang the kernel): it then records FSTAT_ERR_TIMEOUT and
+// the kernel returns.
+constexpr int kWaitLimit = 1 << 22;
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// order this thread's earlier shared-memory accesses before async-proxy writes
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+          "r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// rows per box of a pass-B tile load (the box height limit is 256)
+constexpr int kTmaRows = 256;
 
 __device__ __forceinline__ int pad_idx(int pos, int ps) { return pos + (pos >> ps); }
 
@@ -560,9 +611,11 @@ __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type*
       }
   }
   Pair<T> v[S::R0];
+  // staged rows: padded positions (per-thread copies) or dense rows (TMA boxes)
+  constexpr bool kDense = (V & 4) != 0;
 #pragma unroll
   for (int s = 0; s < S::R0; ++s)
-    v[s] = STAGED ? pload(buf + pad_idx(t + s * S::TPC, S::PS) * CB)
+    v[s] = STAGED ? pload(buf + (kDense ? t + s * S::TPC : pad_idx(t + s * S::TPC, S::PS)) * CB)
                   : pload_g(Z + (int64_t)(t + s * S::TPC) * n2 + k2);
   if constexpr (STAGED) __syncthreads();  // the staged rows are overwritten below
   dft<T, S::R0>(v);
@@ -604,11 +657,11 @@ template <typename T, int L, int CB, int V, int MODE>
 __global__ void __launch_bounds__(CB * Shape<T, L, V>::TPC, (min_blocks<T, L, CB, V>()))
 k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
          const typename TwT<T>::type* __restrict__ twL, const SkyConst* __restrict__ sky,
-         float* __restrict__ out, const PeakArgs pk) {
+         float* __restrict__ out, const PeakArgs pk, const __grid_constant__ CUtensorMap zmap) {
   using S = Shape<T, L, V>;
   using B = Buf<T, L, CB, V>;
   using PM = typename PairMem<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   PM* smem = reinterpret_cast<PM*>(smem_raw);
   const int c = threadIdx.x % CB;
   const int t = threadIdx.x / CB;
@@ -630,6 +683,67 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
   }
   if constexpr (!kPipeline) {
     pass_b_tile<T, L, CB, V, false, MODE>(blockIdx.x, smem + c, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks);
+  } else if constexpr ((V & 4) != 0) {
+    // Tiles by bulk tensor copies: thread 0 loads tile k's CB columns of
+    // all L rows as boxes of kTmaRows rows into stage k mod NBUF, counted
+    // on that stage's mbarrier; use u of a stage completes phase u.
+    __shared__ unsigned long long s_bar[2];
+    const int n_tiles = n2 / CB;
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bar[0], 1);
+      mbar_init(&s_bar[1], 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    unsigned issued[2] = {0u, 0u};  // loads issued per stage (thread 0)
+    unsigned waited[2] = {0u, 0u};  // loads waited for per stage (every thread)
+    auto issue = [&](int tl, int b) {
+      PM* dst = smem + b * (CB * S::LP);
+      fence_proxy_async();  // the stage's earlier reads and writes precede the copy
+      mbar_expect_tx(&s_bar[b], (unsigned)(L * CB * sizeof(PM)));
+#pragma unroll 1
+      for (int r = 0; r < L; r += kTmaRows)
+        tma_load_2d(dst + r * CB, &zmap, tl * CB * (int)(sizeof(PM) / sizeof(float)), r, &s_bar[b]);
+      ++issued[b];
+    };
+    int tile = blockIdx.x;
+    if (threadIdx.x == 0 && tile < n_tiles) issue(tile, 0);
+    bool all_ok = true;  // CTA-wide: every thread's wait succeeded
+    int it = 0;
+    for (; tile < n_tiles; ++it, tile += gridDim.x) {
+      const int b = B::NBUF == 2 ? (it & 1) : 0;
+      if (threadIdx.x == 0) {
+        if constexpr (B::NBUF == 2) {
+          if (tile + (int)gridDim.x < n_tiles) issue(tile + gridDim.x, b ^ 1);
+        } else {
+          if (it > 0) issue(tile, 0);  // the previous tile released the only stage
+        }
+      }
+      const bool ok = mbar_wait(&s_bar[b], waited[b] & 1u);
+      if (ok) ++waited[b];
+      all_ok = __syncthreads_and(ok) != 0;
+      if (!all_ok) break;
+      pass_b_tile<T, L, CB, V, true, MODE>(tile, smem + b * (CB * S::LP) + c, c, t, Z, n2, twL, kA, kB, kC,
+                                           out, pk, ks);
+      fence_proxy_async();  // this thread's accesses to the stage precede the next bulk copy into it
+      __syncthreads();      // this stage is the load target NBUF tiles on
+    }
+    if (!all_ok) {
+      // a wait ran out: record it, then give the loads still in flight a
+      // bounded chance to land before the CTA's shared memory goes away
+      if (threadIdx.x == 0) {
+        if (pk.err) atomicCAS(pk.err, 0, FSTAT_ERR_TIMEOUT);
+        for (int b = 0; b < 2; ++b)
+          for (unsigned u = waited[b]; u < issued[b]; ++u) mbar_wait(&s_bar[b], u & 1u);
+      }
+      return;
+    }
+    if constexpr (MODE == kPeaks) {
+      if (ks) {  // the loop ended on a barrier: every tile's keys are in
+        for (int b = threadIdx.x; b < n_bands; b += blockDim.x)
+          if (ks[b]) atomicMax(pk.band_key + b, ks[b]);
+      }
+    }
   } else {
     const int n_tiles = n2 / CB;
     auto stage = [&](int it) { return smem + (B::NBUF == 2 ? (it & 1) : 0) * (CB * S::LP) + c; };
@@ -717,6 +831,44 @@ cudaError_t run_a(const void* G, int64_t lc, int64_t n, int n1, const void* twA,
   return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled, through the runtime's driver entry point (the
+// library does not link the driver API).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+inline EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
+
+// Tensor map of pass B's input (FP32 pairs): L rows of n2 pairs, i.e. rows
+// of 4 n2 floats at a pitch of 16 n2 bytes; a box is CB pairs (16 CB bytes,
+// a multiple of 16) by min(L, kTmaRows) rows.  Box x coordinates are
+// multiples of 4 CB floats, so every copy starts on a 16-byte boundary.
+inline cudaError_t z_tensor_map(CUtensorMap* map, const void* Z, int L, int n2, int CB) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  if (((uintptr_t)Z & 15) || CB * 4 > 256) return cudaErrorInvalidValue;
+  const cuuint64_t dims[2] = {(cuuint64_t)n2 * 4, (cuuint64_t)L};
+  const cuuint64_t strides[1] = {(cuuint64_t)n2 * 16};
+  const cuuint32_t box[2] = {(cuuint32_t)(CB * 4), (cuuint32_t)(L < kTmaRows ? L : kTmaRows)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(Z), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <typename T, int L, int CB, int V, int MODE>
 cudaError_t run_b(const void* Z, int n2, const void* twB, const SkyConst* sky, float* out, const PeakArgs& pk,
                   cudaStream_t st, int res) {
@@ -733,8 +885,16 @@ cudaError_t run_b(const void* Z, int n2, const void* twB, const SkyConst* sky, f
   if (n2 % CB) return cudaErrorInvalidConfiguration;
   const int tiles = n2 / CB;
   const int grid = persistent_grid(tiles, ctas, per_sm, res);
+  CUtensorMap zmap;
+  memset(&zmap, 0, sizeof(zmap));
+  if constexpr ((V & 4) != 0) {
+    static_assert(sizeof(T) == 4 && kPipeline, "TMA tiles: FP32, persistent pass");
+    static_assert(L * CB * sizeof(typename S::PM) < (1u << 20), "mbarrier transaction count");
+    const cudaError_t e = z_tensor_map(&zmap, Z, L, n2, CB);
+    if (e != cudaSuccess) return e;
+  }
   k_pass_b<T, L, CB, V, MODE><<<grid, threads, smem, st>>>(
-      (const typename S::PM*)Z, n2, (const typename S::TW*)twB, sky, out, pk);
+      (const typename S::PM*)Z, n2, (const typename S::TW*)twB, sky, out, pk, zmap);
   return cudaGetLastError();
 }
 
@@ -798,6 +958,12 @@ cudaError_t pick_b(int cb, int v, const void* Z, int n2, const void* twB, const 
     if constexpr (L >= 1024) {
       if (v == 1) return pick_b_v<T, L, 1, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
       if (v == 3) return pick_b_v<T, L, 3, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
+      if constexpr (kPipeline) {  // tiles by bulk tensor copies
+        if (v == 4) return pick_b_v<T, L, 4, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
+        if (v == 5) return pick_b_v<T, L, 5, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
+        if (v == 6) return pick_b_v<T, L, 6, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
+        if (v == 7) return pick_b_v<T, L, 7, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
+      }
     }
   }
   return cudaErrorInvalidConfiguration;

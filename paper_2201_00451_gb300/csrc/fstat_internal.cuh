@@ -159,6 +159,7 @@ struct PeakArgs {
   float thr;
   int log2_band;                 // log2(bins per band)
   int shift;                     // accumulate: bin m adds to bin m - shift
+  int* err;                      // where a pass records FSTAT_ERR_TIMEOUT, or nullptr
 };
 
 // Band key: order-preserving image of the float 2F in the high word, the
@@ -178,24 +179,27 @@ cudaError_t launch_pass_a_f32(int log2_n2, int ca, int va, const void* G, int64_
                               const void* twA, const void* hi, const void* lo, int h, const TmplCoef* coef,
                               void* Z, cudaStream_t st, int res = 0);
 // pk == nullptr: write 2F to out[n_fft]; otherwise reduce it as pk says.
+// err: where a pass records a timed-out wait (FSTAT_ERR_TIMEOUT), or nullptr
 cudaError_t launch_pass_b_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                               const SkyConst* sky, float* out, cudaStream_t st,
-                              const PeakArgs* pk = nullptr, int res = 0);
+                              const PeakArgs* pk = nullptr, int res = 0, int* err = nullptr);
 cudaError_t launch_pass_a_f64(int log2_n2, int ca, int va, const void* G, int64_t lc, int64_t n, int n1,
                               const void* twA, const void* hi, const void* lo, int h, const TmplCoef* coef,
                               void* Z, cudaStream_t st, int res = 0);
 cudaError_t launch_pass_b_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                               const SkyConst* sky, float* out, cudaStream_t st,
-                              const PeakArgs* pk = nullptr, int res = 0);
+                              const PeakArgs* pk = nullptr, int res = 0, int* err = nullptr);
 cudaError_t launch_pass_b_peak_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                                    const SkyConst* sky, const PeakArgs& pk, cudaStream_t st, int res = 0);
 cudaError_t launch_pass_b_peak_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                                    const SkyConst* sky, const PeakArgs& pk, cudaStream_t st, int res = 0);
 // Accumulate mode: out[m - shift] += 2F[m] for 0 <= m - shift < n_fft.
 cudaError_t launch_pass_b_acc_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
-                                  const SkyConst* sky, float* out, int shift, cudaStream_t st, int res = 0);
+                                  const SkyConst* sky, float* out, int shift, cudaStream_t st, int res = 0,
+                                  int* err = nullptr);
 cudaError_t launch_pass_b_acc_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
-                                  const SkyConst* sky, float* out, int shift, cudaStream_t st, int res = 0);
+                                  const SkyConst* sky, float* out, int shift, cudaStream_t st, int res = 0,
+                                  int* err = nullptr);
 // Band keys of n rows x n_bands -> maximum 2F and its bin (band_bin may be null).
 cudaError_t launch_band_decode(const unsigned long long* keys, int64_t count, float* band_max,
                                int32_t* band_bin, cudaStream_t st);

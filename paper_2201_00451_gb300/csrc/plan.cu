@@ -69,7 +69,8 @@ struct fstat_plan {
   void* tw = nullptr;            // twiddle tables for the current split
   TwiddleTables tt{};
   int ca = 0, cb = 0;            // CTA shapes of pass A / pass B (0 = default)
-  int va = 0, vb = 0;            // schedules of pass A / pass B (bit 0 radix-8 first, bit 1 one buffer)
+  int va = 0, vb = 0;            // schedules of pass A / pass B (bit 0 radix-8 first, bit 1 one buffer,
+                                 // bit 2 pass B tile loads by TMA)
   int ra = 0, rb = 0;            // persistent CTAs per SM of pass A / pass B (0 = all resident)
   int* d_err = nullptr;   // [0] sticky kernel error, [1] scratch for input checks
   int* h_err = nullptr;   // pinned
@@ -239,15 +240,15 @@ cudaError_t launch_b(fstat_plan* p, int cb, int vb, float* out, cudaStream_t st,
   if (!Z) Z = p->Z;
   if (res < 0) res = p->rb;
   return p->d.precision == FSTAT_FP64
-      ? launch_pass_b_f64(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk, res)
-      : launch_pass_b_f32(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk, res);
+      ? launch_pass_b_f64(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk, res, p->d_err)
+      : launch_pass_b_f32(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk, res, p->d_err);
 }
 
 cudaError_t launch_b_acc(fstat_plan* p, float* out, int shift, cudaStream_t st, void* Z) {
   const TwiddleTables& t = p->tt;
   return p->d.precision == FSTAT_FP64
-      ? launch_pass_b_acc_f64(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st, p->rb)
-      : launch_pass_b_acc_f32(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st, p->rb);
+      ? launch_pass_b_acc_f64(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st, p->rb, p->d_err)
+      : launch_pass_b_acc_f32(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st, p->rb, p->d_err);
 }
 
 }  // namespace
@@ -264,6 +265,7 @@ const char* fstat_strerror(int code) {
     case FSTAT_ERR_NONFINITE: return "non-finite value in input series";
     case FSTAT_ERR_NOT_READY: return "not every detector has data";
     case FSTAT_ERR_UNSUPPORTED: return "size outside the supported range";
+    case FSTAT_ERR_TIMEOUT: return "a kernel's bounded wait for its own copies ran out";
     default: return "unknown error";
   }
 }
@@ -965,7 +967,7 @@ int fstat_get_residency(const fstat_plan* p, int* ra, int* rb) {
 }
 
 int fstat_set_cta(fstat_plan* p, int ca, int va, int cb, int vb) {
-  if (!p || ca < 0 || cb < 0 || ca > 32 || cb > 32 || va < 0 || va > 3 || vb < 0 || vb > 3)
+  if (!p || ca < 0 || cb < 0 || ca > 32 || cb > 32 || va < 0 || va > 3 || vb < 0 || vb > 7)
     return FSTAT_ERR_INVALID_ARG;
   p->ca = ca;
   p->va = va;
@@ -1093,8 +1095,11 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
     launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, 0, kPipe, p->d_coef, st);
     // isolated timings of every compiled shape of each pass
     std::vector<std::pair<float, std::pair<int, int>>> ta, tb;
-    for (int v = 0; v < 4; ++v) {  // schedules: radix-8 first (bit 0), one buffer (bit 1)
+    // schedules: radix-8 first (bit 0), one buffer (bit 1), and for pass B
+    // tile loads by the tensor-memory-access engine (bit 2)
+    for (int v = 0; v < 8; ++v) {
       for (int c : kCa) {
+        if (v > 3) break;
         float ms = time_pass(p, 0, c, v, p->d_coef, out, st, e0, e1);
         if (ms > 0.f) ta.push_back({ms, {c, v}});
       }

@@ -46,9 +46,11 @@ def test_every_split_and_cta_shape(log2n, n):
             plan.set_data(X, x[X], t.sigmas[X])
         for l1 in range(max(5, log2n - 12), min(12, log2n - 5) + 1):
             plan.set_split(1 << l1)
-            for v in (0, 1, 2, 3):   # radix-8 first (bit 0), one shared buffer (bit 1)
+            # radix-8 first (bit 0), one shared buffer (bit 1), pass B tile
+            # loads by TMA (bit 2, rows of 1024 points or more)
+            for v in range(8):
                 for ca, cb in [(0, 0), (1, 1), (2, 2), (4, 4), (1, 8), (2, 8)]:
-                    plan.set_cta(ca, cb, v, v)
+                    plan.set_cta(ca, cb, v & 3, v)
                     try:
                         out = plan.compute(tm)[0].cpu().numpy()
                     except pkg.FstatError as e:
