@@ -58,9 +58,11 @@ template <> struct TwT<double> { using type = double2; };
 // V = 0: radix-16 first (fewest shared-memory passes, 16 points per thread);
 // Schedule code V: bit 0 (lengths >= 1024) = radix-8 first (8 points per
 // thread, half the registers, one more pass); bit 1 = one shared buffer
-// (no prefetch), half the shared memory, so that a CTA of each pass fits
-// on one SM; bit 2 (pass B) = tiles loaded by bulk tensor copies (TMA)
-// instead of per-thread 16-byte copies.  The first radix is the largest.
+// (no prefetch), half the shared memory, and for radix-16 CTAs of up to
+// 256 threads a register cap (128) that lets two CTAs share an SM; bit 3
+// (pass A, with bit 1, radix-16) = a tighter cap (80) for three CTAs per
+// SM; bit 2 (pass B) = tiles loaded by bulk tensor copies (TMA) instead of
+// per-thread 16-byte copies.  The first radix is the largest.
 __host__ __device__ constexpr bool r8(int L, int V) { return (V & 1) && L >= 1024; }
 __host__ __device__ constexpr int np_of(int L, int V) { return r8(L, V) ? 4 : (L <= 256 ? 2 : 3); }
 __host__ __device__ constexpr int r_of(int L, int p, int V) {
@@ -424,9 +426,12 @@ __device__ __forceinline__ void pass_a_tile(int tile, typename PairMem<T>::type*
 }
 
 template <typename T, int L, int C, int V> constexpr int min_blocks() {
-  // radix-8 variants: ask for enough resident CTAs to cap registers at 64
+  // radix-8 variants: ask for enough resident CTAs to cap registers at 64;
+  // one-buffer radix-16 variants of up to 256 threads: two CTAs per SM
+  // (three with bit 3), which their shared memory allows
   constexpr int threads = C * Shape<T, L, V>::TPC;
   constexpr int want = 65536 / (threads * 64);
+  if constexpr ((V & 1) == 0 && (V & 2) != 0) return threads <= 256 ? ((V & 8) ? 3 : 2) : 1;
   return ((V & 1) && kR8MinBlocks > 0 && want > 1) ? want : 1;
 }
 
@@ -928,6 +933,7 @@ cudaError_t pick_a(int ca, int v, const void* G, int64_t lc, int64_t n, int n1, 
     if constexpr (L >= 1024) {
       if (v == 1) return pick_a_v<T, L, 1>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
       if (v == 3) return pick_a_v<T, L, 3>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
+      if (v == 10) return pick_a_v<T, L, 10>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
     }
   }
   return cudaErrorInvalidConfiguration;

@@ -70,7 +70,7 @@ struct fstat_plan {
   TwiddleTables tt{};
   int ca = 0, cb = 0;            // CTA shapes of pass A / pass B (0 = default)
   int va = 0, vb = 0;            // schedules of pass A / pass B (bit 0 radix-8 first, bit 1 one buffer,
-                                 // bit 2 pass B tile loads by TMA)
+                                 // bit 2 pass B tile loads by TMA, bit 3 pass A three CTAs per SM)
   int ra = 0, rb = 0;            // persistent CTAs per SM of pass A / pass B (0 = all resident)
   int* d_err = nullptr;   // [0] sticky kernel error, [1] scratch for input checks
   int* h_err = nullptr;   // pinned
@@ -967,7 +967,7 @@ int fstat_get_residency(const fstat_plan* p, int* ra, int* rb) {
 }
 
 int fstat_set_cta(fstat_plan* p, int ca, int va, int cb, int vb) {
-  if (!p || ca < 0 || cb < 0 || ca > 32 || cb > 32 || va < 0 || va > 3 || vb < 0 || vb > 7)
+  if (!p || ca < 0 || cb < 0 || ca > 32 || cb > 32 || va < 0 || (va > 3 && va != 10) || vb < 0 || vb > 7)
     return FSTAT_ERR_INVALID_ARG;
   p->ca = ca;
   p->va = va;
@@ -1095,14 +1095,17 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
     launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, 0, kPipe, p->d_coef, st);
     // isolated timings of every compiled shape of each pass
     std::vector<std::pair<float, std::pair<int, int>>> ta, tb;
-    // schedules: radix-8 first (bit 0), one buffer (bit 1), and for pass B
-    // tile loads by the tensor-memory-access engine (bit 2)
-    for (int v = 0; v < 8; ++v) {
+    // schedules: radix-8 first (bit 0), one buffer (bit 1), for pass B tile
+    // loads by the tensor-memory-access engine (bit 2), for pass A three
+    // CTAs per SM (bit 3)
+    static const int kVa[] = {0, 1, 2, 3, 10};
+    for (int v : kVa) {
       for (int c : kCa) {
-        if (v > 3) break;
         float ms = time_pass(p, 0, c, v, p->d_coef, out, st, e0, e1);
         if (ms > 0.f) ta.push_back({ms, {c, v}});
       }
+    }
+    for (int v = 0; v < 8; ++v) {
       for (int c : kCb) {
         float ms = time_pass(p, 1, c, v, p->d_coef, out, st, e0, e1);
         if (ms > 0.f) tb.push_back({ms, {c, v}});

@@ -47,16 +47,18 @@ def test_every_split_and_cta_shape(log2n, n):
         for l1 in range(max(5, log2n - 12), min(12, log2n - 5) + 1):
             plan.set_split(1 << l1)
             # radix-8 first (bit 0), one shared buffer (bit 1), pass B tile
-            # loads by TMA (bit 2, rows of 1024 points or more)
-            for v in range(8):
+            # loads by TMA (bit 2, rows of 1024 points or more), pass A
+            # three CTAs per SM (va 10)
+            for v in range(9):
+                va, vb = (10, 2) if v == 8 else (v & 3, v)
                 for ca, cb in [(0, 0), (1, 1), (2, 2), (4, 4), (1, 8), (2, 8)]:
-                    plan.set_cta(ca, cb, v & 3, v)
+                    plan.set_cta(ca, cb, va, vb)
                     try:
                         out = plan.compute(tm)[0].cpu().numpy()
                     except pkg.FstatError as e:
                         assert e.code == -3  # shape not compiled for this length
                         continue
-                    assert _ok(out, ref), (l1, ca, cb, v)
+                    assert _ok(out, ref), (l1, ca, cb, va, vb)
                     ran += 1
         plan.sync()
     assert ran >= 3

@@ -230,3 +230,26 @@ def test_residency_caps_and_single_buffer_schedules_give_identical_2F():
         with pytest.raises(pkg.FstatError):
             plan.set_residency(-1, 0)
     assert_parity(base, resamp.fstat(t, x, tm))
+
+
+def test_register_caps_and_tma_loads_give_identical_2F():
+    # Radix-16 schedules that differ only in buffering, register cap (two
+    # or three CTAs per SM) and how pass B's tiles arrive in shared memory
+    # (cp.async or TMA) run the same arithmetic: bitwise equal 2F.
+    t = small(seed=13, n_fft=1 << 20, n_samples=400_003, dt=1.0)
+    x = synth.make_data(t)
+    tm = t.templates()[:3]
+    with pkg.FstatPlan.from_target(t) as plan:
+        for X in range(2):
+            plan.set_data(X, x[X], t.sigmas[X])
+        plan.set_split(1024)           # pass A 1024 points, pass B 1024 points
+        plan.set_cta(1, 4, 0, 0)
+        base = plan.compute(tm).cpu().numpy()
+        for ca, cb, va, vb in ((1, 4, 2, 2), (1, 4, 10, 4), (1, 4, 10, 6), (1, 2, 2, 6), (2, 8, 2, 4)):
+            plan.set_cta(ca, cb, va, vb)
+            assert plan.cta == (ca, va, cb, vb)
+            assert np.array_equal(plan.compute(tm).cpu().numpy(), base), (ca, cb, va, vb)
+        for bad in ((1, 4, 4, 0), (1, 4, 11, 0), (1, 4, 0, 8)):
+            with pytest.raises(pkg.FstatError):
+                plan.set_cta(*bad)
+    assert_parity(base, resamp.fstat(t, x, tm))
