@@ -21,9 +21,9 @@
 // chosen per FFT length by the autotuner.
 #pragma once
 
-#include <cuda.h>  // CUtensorMap
+#include <cuda.h>  // CUtensorMap (encoded through the runtime's driver entry point)
 #include <stdint.h>
-#include <string.h> (the tensor map is encoded through the runtime's driver entry point)
+#include <string.h>
 
 #include "fstat_internal.cuh"
 
@@ -276,9 +276,14 @@ template <typename T, int R> __device__ __forceinline__ void dft(Pair<T>* x) {
 // 1..NP-1.  On return v holds the last pass's outputs: butterfly
 // b = t + q * TPC, output index b + s * NSL in v[q * RL + s].
 // Shared-memory address of logical position pos is pad(pos) * STRIDE.
-template <typename T, int L, int V, int STRIDE, int P, bool TABLE>
+// at_free() runs once the last pass has read the buffer into registers (all
+// threads past the barrier that follows): the buffer is free from there on.
+struct NoOp {
+  __device__ __forceinline__ void operator()() const {}
+};
+template <typename T, int L, int V, int STRIDE, int P, bool TABLE, typename F = NoOp>
 __device__ __forceinline__ void passes(Pair<T>* v, typename PairMem<T>::type* buf, int t,
-                                       const typename TwT<T>::type* __restrict__ twL) {
+                                       const typename TwT<T>::type* __restrict__ twL, const F& at_free = F()) {
   using S = Shape<T, L, V>;
   constexpr int R = r_of(L, P, V);
   constexpr int NS = ns_of(L, P, V);
@@ -291,6 +296,7 @@ __device__ __forceinline__ void passes(Pair<T>* v, typename PairMem<T>::type* bu
     for (int s = 0; s < R; ++s) v[q * R + s] = pload(buf + pad_idx(b + s * (L / R), S::PS) * STRIDE);
   }
   __syncthreads();
+  if constexpr (P + 1 == S::NP) at_free();
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int b = t + q * S::TPC;
@@ -319,7 +325,7 @@ __device__ __forceinline__ void passes(Pair<T>* v, typename PairMem<T>::type* bu
       for (int s = 0; s < R; ++s) pstore(buf + pad_idx(base + s * NS, S::PS) * STRIDE, v[q * R + s]);
     }
     __syncthreads();
-    passes<T, L, V, STRIDE, P + 1, TABLE>(v, buf, t, twL);
+    passes<T, L, V, STRIDE, P + 1, TABLE, F>(v, buf, t, twL, at_free);
   }
 }
 
@@ -374,12 +380,12 @@ __device__ __forceinline__ void spin_rot(const TmplCoef& c, int si, double* cs, 
 // One tile = CA columns.  `staged`: the column samples were copied to `buf`
 // (at padded natural positions) by cp.async; otherwise they are loaded from
 // global memory straight into registers.
-template <typename T, int L, int CA, int V, bool STAGED>
+template <typename T, int L, int CA, int V, bool STAGED, typename F = NoOp>
 __device__ __forceinline__ void pass_a_tile(int tile, typename PairMem<T>::type* buf, int c, int t,
                                             const typename PairMem<T>::type* __restrict__ G, int64_t lc,
                                             int n, int n1, const typename TwT<T>::type* __restrict__ twL,
                                             const TmplCoef& tc, T inv_n,
-                                            typename PairMem<T>::type* __restrict__ Z) {
+                                            typename PairMem<T>::type* __restrict__ Z, const F& at_free = F()) {
   using S = Shape<T, L, V>;
   using PM = typename PairMem<T>::type;
   const int col = tile * CA + c;
@@ -401,7 +407,7 @@ __device__ __forceinline__ void pass_a_tile(int tile, typename PairMem<T>::type*
   if constexpr (STAGED) __syncthreads();  // the staged column is overwritten below
   dft<T, S::R0>(v);
   store_pass0<T, L, V, 1>(v, buf, t);
-  passes<T, L, V, 1, 1, false>(v, buf, t, twL);
+  passes<T, L, V, 1, 1, false, F>(v, buf, t, twL, at_free);
 
   // four-step twiddle W_N^{col k2} = W_N^{col b} (W_N^{col NSL})^s for
   // k2 = b + s * NSL, and store Z[col][k2]
@@ -438,7 +444,8 @@ template <typename T, int L, int C, int V> constexpr int min_blocks() {
 // Direct mode (kPipeline = false): one tile per CTA.  Pipelined mode: the
 // CTA transforms tiles b, b + grid, ...; the next tile's samples are copied
 // asynchronously into the other buffer while the current one is
-// transformed in place.
+// transformed in place, or, with one buffer, into that buffer as soon as
+// the last Stockham pass has read it (under that pass and the epilogue).
 template <typename T, int L, int CA, int V>
 __global__ void __launch_bounds__(CA * Shape<T, L, V>::TPC, (min_blocks<T, L, CA, V>()))
 k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int n1,
@@ -447,7 +454,7 @@ k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int
   using S = Shape<T, L, V>;
   using B = Buf<T, L, CA, V>;
   using PM = typename PairMem<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   PM* smem = reinterpret_cast<PM*>(smem_raw);
   const int c = threadIdx.x / S::TPC;
   const int t = threadIdx.x % S::TPC;
@@ -469,24 +476,30 @@ k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int
       }
     };
     int tile = blockIdx.x;
-    if constexpr (B::NBUF == 2) {
-      if (tile < n_tiles) prefetch(tile, stage(0));
-      cp_async_commit();
-    }
+    if (tile < n_tiles) prefetch(tile, stage(0));
+    cp_async_commit();
     for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
       PM* buf = stage(it);
+      const int next = tile + gridDim.x;
       if constexpr (B::NBUF == 2) {
-        if (tile + (int)gridDim.x < n_tiles) prefetch(tile + gridDim.x, stage(it + 1));
+        if (next < n_tiles) prefetch(next, stage(it + 1));
         cp_async_commit();
         cp_async_wait<1>();
       } else {
-        prefetch(tile, buf);
-        cp_async_commit();
         cp_async_wait<0>();
       }
       __syncthreads();
-      pass_a_tile<T, L, CA, V, true>(tile, buf, c, t, G, lc, n, n1, twL, tc, inv_n, Z);
-      __syncthreads();  // this buffer is the prefetch target two tiles on
+      if constexpr (B::NBUF == 2) {
+        pass_a_tile<T, L, CA, V, true>(tile, buf, c, t, G, lc, n, n1, twL, tc, inv_n, Z);
+        __syncthreads();  // this buffer is the prefetch target two tiles on
+      } else {
+        // no barrier after the tile: it stopped reading the buffer before
+        // the barrier at which the next tile's copies were issued
+        pass_a_tile<T, L, CA, V, true>(tile, buf, c, t, G, lc, n, n1, twL, tc, inv_n, Z, [&] {
+          if (next < n_tiles) prefetch(next, buf);
+          cp_async_commit();
+        });
+      }
     }
   }
 }
@@ -593,12 +606,12 @@ __device__ __forceinline__ void peak_epilogue(const float* sf, int k2_0, int n2,
   }
 }
 
-template <typename T, int L, int CB, int V, bool STAGED, int MODE>
+template <typename T, int L, int CB, int V, bool STAGED, int MODE, typename F = NoOp>
 __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type* buf, int c, int t,
                                             const typename PairMem<T>::type* __restrict__ Z, int n2,
                                             const typename TwT<T>::type* __restrict__ twL, T kA, T kB, T kC,
                                             float* __restrict__ out, const PeakArgs& pk,
-                                            unsigned long long* ks) {
+                                            unsigned long long* ks, const F& at_free = F()) {
   using S = Shape<T, L, V>;
   const int k2 = tile * CB + c;
   constexpr int NB = S::R0 / S::RL;
@@ -625,7 +638,7 @@ __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type*
   if constexpr (STAGED) __syncthreads();  // the staged rows are overwritten below
   dft<T, S::R0>(v);
   store_pass0<T, L, V, CB>(v, buf, t);
-  passes<T, L, V, CB, 1, kPassBTable && sizeof(T) == 4>(v, buf, t, twL);
+  passes<T, L, V, CB, 1, kPassBTable && sizeof(T) == 4, F>(v, buf, t, twL, at_free);
 
   float* sf = reinterpret_cast<float*>(buf - c);  // the CTA's stage, reused by the peaks epilogue
   if constexpr (MODE == kPeaks) __syncthreads();  // every thread is done with the exchange buffer
@@ -691,7 +704,10 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
   } else if constexpr ((V & 4) != 0) {
     // Tiles by bulk tensor copies: thread 0 loads tile k's CB columns of
     // all L rows as boxes of kTmaRows rows into stage k mod NBUF, counted
-    // on that stage's mbarrier; use u of a stage completes phase u.
+    // on that stage's mbarrier; use u of a stage completes phase u.  With
+    // one stage (and no peaks epilogue, which reuses it) the next tile's
+    // copies start as soon as the last Stockham pass has read the stage.
+    constexpr bool kEarly = B::NBUF == 1 && MODE != kPeaks;
     __shared__ unsigned long long s_bar[2];
     const int n_tiles = n2 / CB;
     if (threadIdx.x == 0) {
@@ -720,7 +736,7 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
       if (threadIdx.x == 0) {
         if constexpr (B::NBUF == 2) {
           if (tile + (int)gridDim.x < n_tiles) issue(tile + gridDim.x, b ^ 1);
-        } else {
+        } else if constexpr (!kEarly) {
           if (it > 0) issue(tile, 0);  // the previous tile released the only stage
         }
       }
@@ -728,10 +744,19 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
       if (ok) ++waited[b];
       all_ok = __syncthreads_and(ok) != 0;
       if (!all_ok) break;
-      pass_b_tile<T, L, CB, V, true, MODE>(tile, smem + b * (CB * S::LP) + c, c, t, Z, n2, twL, kA, kB, kC,
-                                           out, pk, ks);
-      fence_proxy_async();  // this thread's accesses to the stage precede the next bulk copy into it
-      __syncthreads();      // this stage is the load target NBUF tiles on
+      if constexpr (kEarly) {
+        // no barrier after the tile: it stopped reading the stage before the
+        // barrier at which thread 0 issued the next tile's copies
+        const int next = tile + gridDim.x;
+        pass_b_tile<T, L, CB, V, true, MODE>(tile, smem + c, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks, [&] {
+          if (threadIdx.x == 0 && next < n_tiles) issue(next, 0);
+        });
+      } else {
+        pass_b_tile<T, L, CB, V, true, MODE>(tile, smem + b * (CB * S::LP) + c, c, t, Z, n2, twL, kA, kB, kC,
+                                             out, pk, ks);
+        fence_proxy_async();  // this thread's accesses to the stage precede the next bulk copy into it
+        __syncthreads();      // this stage is the load target NBUF tiles on
+      }
     }
     if (!all_ok) {
       // a wait ran out: record it, then give the loads still in flight a
@@ -760,25 +785,40 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
         cp_pair(dst + pad_idx(n1, S::PS) * CB, Z + (int64_t)n1 * n2 + k2);
       }
     };
+    // with one buffer (and no peaks epilogue, which reuses it) the next
+    // tile's copies start as soon as the last Stockham pass has read it
+    constexpr bool kEarly = B::NBUF == 1 && MODE != kPeaks;
     int tile = blockIdx.x;
-    if constexpr (B::NBUF == 2) {
+    if constexpr (B::NBUF == 2 || kEarly) {
       if (tile < n_tiles) prefetch(tile, stage(0));
       cp_async_commit();
     }
     for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
       PM* buf = stage(it);
+      const int next = tile + gridDim.x;
       if constexpr (B::NBUF == 2) {
-        if (tile + (int)gridDim.x < n_tiles) prefetch(tile + gridDim.x, stage(it + 1));
+        if (next < n_tiles) prefetch(next, stage(it + 1));
         cp_async_commit();
         cp_async_wait<1>();
+      } else if constexpr (kEarly) {
+        cp_async_wait<0>();
       } else {
         prefetch(tile, buf);
         cp_async_commit();
         cp_async_wait<0>();
       }
       __syncthreads();
-      pass_b_tile<T, L, CB, V, true, MODE>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks);
-      __syncthreads();  // this buffer is the prefetch target two tiles on
+      if constexpr (kEarly) {
+        // no barrier after the tile: it stopped reading the buffer before
+        // the barrier at which the next tile's copies were issued
+        pass_b_tile<T, L, CB, V, true, MODE>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks, [&] {
+          if (next < n_tiles) prefetch(next, buf);
+          cp_async_commit();
+        });
+      } else {
+        pass_b_tile<T, L, CB, V, true, MODE>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks);
+        __syncthreads();  // this buffer is the prefetch target two tiles on
+      }
     }
     if constexpr (MODE == kPeaks) {
       if (ks) {  // the loop ended on a barrier: every tile's keys are in
