@@ -264,11 +264,63 @@ template <typename T> __device__ __forceinline__ void dft16(Pair<T>* x) {
   for (int k = 0; k < 8; ++k) { x[k] = padd(e[k], o[k]); x[k + 8] = psub(e[k], o[k]); }
 }
 
+// The same transforms when the upper half of the inputs is zero (x[R/2..R)
+// unread): the zero-padded first pass of pass A when every column holds at
+// most L/2 samples.  Same output order as dft4/dft8/dft16; the first
+// add/subtract level of the even/odd split drops out.
+template <typename T> __device__ __forceinline__ void dft4_half(Pair<T>& x0, Pair<T>& x1, Pair<T>& x2,
+                                                               Pair<T>& x3) {
+  const Pair<T> a = x0, t3 = pmul_mi(x1);
+  x2 = psub(a, x1);
+  x0 = padd(a, x1);
+  x1 = padd(a, t3);
+  x3 = psub(a, t3);
+}
+template <typename T> __device__ __forceinline__ void dft8_half(Pair<T>* x) {
+  Pair<T> e0 = x[0], e1 = x[2], e2, e3;
+  Pair<T> o0 = x[1], o1 = x[3], o2, o3;
+  dft4_half(e0, e1, e2, e3);
+  dft4_half(o0, o1, o2, o3);
+  o1 = w8_1(o1);
+  o2 = pmul_mi(o2);
+  o3 = w8_3(o3);
+  x[0] = padd(e0, o0); x[4] = psub(e0, o0);
+  x[1] = padd(e1, o1); x[5] = psub(e1, o1);
+  x[2] = padd(e2, o2); x[6] = psub(e2, o2);
+  x[3] = padd(e3, o3); x[7] = psub(e3, o3);
+}
+template <typename T> __device__ __forceinline__ void dft16_half(Pair<T>* x) {
+  Pair<T> e[8], o[8];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { e[k] = x[2 * k]; o[k] = x[2 * k + 1]; }
+  dft8_half(e);
+  dft8_half(o);
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;  // cos, sin of pi/8
+  o[1] = pmul(o[1], c1, -s1);
+  o[2] = w8_1(o[2]);
+  o[3] = pmul(o[3], s1, -c1);
+  o[4] = pmul_mi(o[4]);
+  o[5] = pmul(o[5], -s1, -c1);
+  o[6] = w8_3(o[6]);
+  o[7] = pmul(o[7], -c1, -s1);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) { x[k] = padd(e[k], o[k]); x[k + 8] = psub(e[k], o[k]); }
+}
 template <typename T, int R> __device__ __forceinline__ void dft(Pair<T>* x) {
   if constexpr (R == 2) { Pair<T> a = x[0], b = x[1]; x[0] = padd(a, b); x[1] = psub(a, b); }
   else if constexpr (R == 4) dft4(x[0], x[1], x[2], x[3]);
   else if constexpr (R == 8) dft8(x);
   else dft16(x);
+}
+
+template <typename T, int R> __device__ __forceinline__ void dft_half(Pair<T>* x) {
+  if constexpr (R == 8) dft8_half(x);
+  else if constexpr (R == 16) dft16_half(x);
+  else {
+#pragma unroll
+    for (int s = R / 2; s < R; ++s) x[s] = pzero<T>();
+    dft<T, R>(x);
+  }
 }
 
 // --------------------------------------------------------- Stockham passes
@@ -391,8 +443,7 @@ __device__ __forceinline__ void pass_a_tile(int tile, typename PairMem<T>::type*
   const int col = tile * CA + c;
   const PM* gcol = G + (int64_t)col * lc;
   Pair<T> v[S::R0];
-#pragma unroll
-  for (int s = 0; s < S::R0; ++s) {
+  auto load = [&](int s) {
     const int n2 = t + s * S::TPC;
     const int j = col + n1 * n2;
     if (j < n) {
@@ -403,9 +454,20 @@ __device__ __forceinline__ void pass_a_tile(int tile, typename PairMem<T>::type*
     } else {
       v[s] = pzero<T>();
     }
+  };
+  // zero padding to at least twice the data (n <= n1 L / 2): no column has
+  // a sample at n2 >= L/2, the upper half of every first butterfly is zero
+  const bool half = (int64_t)n1 * (L / 2) >= (int64_t)n;
+  if (half) {
+#pragma unroll
+    for (int s = 0; s < S::R0 / 2; ++s) load(s);
+  } else {
+#pragma unroll
+    for (int s = 0; s < S::R0; ++s) load(s);
   }
   if constexpr (STAGED) __syncthreads();  // the staged column is overwritten below
-  dft<T, S::R0>(v);
+  if (half) dft_half<T, S::R0>(v);
+  else dft<T, S::R0>(v);
   store_pass0<T, L, V, 1>(v, buf, t);
   passes<T, L, V, 1, 1, false, F>(v, buf, t, twL, at_free);
 
