@@ -113,10 +113,16 @@ template <typename T, int L, int C, int V = 0> struct Buf {
 constexpr int kPeakBands = 1024;
 // pass-B epilogues: store 2F, reduce it (peaks), add it to a shifted row
 constexpr int kStore = 0, kPeaks = 1, kAccumulate = 2;
+// With one buffer the tile's 2F goes to a region of its own (SEP, when it
+// fits) instead of the buffer, so that the next tile's copies can start
+// early as in the other epilogues.  Layout: buffers, band keys, 2F tile.
 template <typename T, int L, int C, int V> struct PeakSmem {
   static constexpr size_t EXTRA = (size_t)kPeakBands * sizeof(unsigned long long);
   static constexpr bool ACC = kPipeline && Buf<T, L, C, V>::BYTES + EXTRA <= 227 * 1024;
-  static constexpr size_t BYTES = Buf<T, L, C, V>::BYTES + (ACC ? EXTRA : 0);
+  static constexpr size_t KEYS_END = Buf<T, L, C, V>::BYTES + (ACC ? EXTRA : 0);
+  static constexpr size_t SF = (size_t)L * C * sizeof(float);
+  static constexpr bool SEP = kPipeline && Buf<T, L, C, V>::NBUF == 1 && KEYS_END + SF <= 227 * 1024;
+  static constexpr size_t BYTES = KEYS_END + (SEP ? SF : 0);
 };
 
 template <typename T, int L, int C, int V = 0> constexpr bool cfg_ok() {
@@ -673,7 +679,7 @@ __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type*
                                             const typename PairMem<T>::type* __restrict__ Z, int n2,
                                             const typename TwT<T>::type* __restrict__ twL, T kA, T kB, T kC,
                                             float* __restrict__ out, const PeakArgs& pk,
-                                            unsigned long long* ks, const F& at_free = F()) {
+                                            unsigned long long* ks, float* sf_sep, const F& at_free = F()) {
   using S = Shape<T, L, V>;
   const int k2 = tile * CB + c;
   constexpr int NB = S::R0 / S::RL;
@@ -702,8 +708,12 @@ __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type*
   store_pass0<T, L, V, CB>(v, buf, t);
   passes<T, L, V, CB, 1, kPassBTable && sizeof(T) == 4, F>(v, buf, t, twL, at_free);
 
-  float* sf = reinterpret_cast<float*>(buf - c);  // the CTA's stage, reused by the peaks epilogue
-  if constexpr (MODE == kPeaks) __syncthreads();  // every thread is done with the exchange buffer
+  // peaks epilogue: the tile's 2F in its own region, or in the CTA's stage
+  // once every thread is done with it as the exchange buffer
+  float* sf = sf_sep ? sf_sep : reinterpret_cast<float*>(buf - c);
+  if constexpr (MODE == kPeaks) {
+    if (!sf_sep) __syncthreads();
+  }
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int b = t + q * S::TPC;
@@ -750,6 +760,9 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
   else { kA = sky->kA; kB = sky->kB; kC = sky->kC; }
   // peaks mode with whole-row bands: this CTA's band keys in shared memory
   unsigned long long* ks = nullptr;
+  float* sf_sep = nullptr;
+  if constexpr (MODE == kPeaks && PeakSmem<T, L, CB, V>::SEP)
+    sf_sep = reinterpret_cast<float*>(smem_raw + PeakSmem<T, L, CB, V>::KEYS_END);
   int n_bands = 0;
   if constexpr (MODE == kPeaks && PeakSmem<T, L, CB, V>::ACC) {
     if (pk.band_key && pk.log2_band >= 31 - __clz(n2)) {
@@ -762,14 +775,15 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
     }
   }
   if constexpr (!kPipeline) {
-    pass_b_tile<T, L, CB, V, false, MODE>(blockIdx.x, smem + c, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks);
+    pass_b_tile<T, L, CB, V, false, MODE>(blockIdx.x, smem + c, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks,
+                                          nullptr);
   } else if constexpr ((V & 4) != 0) {
     // Tiles by bulk tensor copies: thread 0 loads tile k's CB columns of
     // all L rows as boxes of kTmaRows rows into stage k mod NBUF, counted
     // on that stage's mbarrier; use u of a stage completes phase u.  With
-    // one stage (and no peaks epilogue, which reuses it) the next tile's
+    // one stage (and no peaks epilogue that reuses it) the next tile's
     // copies start as soon as the last Stockham pass has read the stage.
-    constexpr bool kEarly = B::NBUF == 1 && MODE != kPeaks;
+    constexpr bool kEarly = B::NBUF == 1 && (MODE != kPeaks || PeakSmem<T, L, CB, V>::SEP);
     __shared__ unsigned long long s_bar[2];
     const int n_tiles = n2 / CB;
     if (threadIdx.x == 0) {
@@ -810,12 +824,13 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
         // no barrier after the tile: it stopped reading the stage before the
         // barrier at which thread 0 issued the next tile's copies
         const int next = tile + gridDim.x;
-        pass_b_tile<T, L, CB, V, true, MODE>(tile, smem + c, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks, [&] {
-          if (threadIdx.x == 0 && next < n_tiles) issue(next, 0);
-        });
+        pass_b_tile<T, L, CB, V, true, MODE>(tile, smem + c, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks, sf_sep,
+                                             [&] {
+                                               if (threadIdx.x == 0 && next < n_tiles) issue(next, 0);
+                                             });
       } else {
         pass_b_tile<T, L, CB, V, true, MODE>(tile, smem + b * (CB * S::LP) + c, c, t, Z, n2, twL, kA, kB, kC,
-                                             out, pk, ks);
+                                             out, pk, ks, sf_sep);
         fence_proxy_async();  // this thread's accesses to the stage precede the next bulk copy into it
         __syncthreads();      // this stage is the load target NBUF tiles on
       }
@@ -831,7 +846,9 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
       return;
     }
     if constexpr (MODE == kPeaks) {
-      if (ks) {  // the loop ended on a barrier: every tile's keys are in
+      if (ks) {
+        if constexpr (kEarly) __syncthreads();  // else the loop ended on one
+        // every tile's keys are in
         for (int b = threadIdx.x; b < n_bands; b += blockDim.x)
           if (ks[b]) atomicMax(pk.band_key + b, ks[b]);
       }
@@ -847,9 +864,9 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
         cp_pair(dst + pad_idx(n1, S::PS) * CB, Z + (int64_t)n1 * n2 + k2);
       }
     };
-    // with one buffer (and no peaks epilogue, which reuses it) the next
+    // with one buffer (and no peaks epilogue that reuses it) the next
     // tile's copies start as soon as the last Stockham pass has read it
-    constexpr bool kEarly = B::NBUF == 1 && MODE != kPeaks;
+    constexpr bool kEarly = B::NBUF == 1 && (MODE != kPeaks || PeakSmem<T, L, CB, V>::SEP);
     int tile = blockIdx.x;
     if constexpr (B::NBUF == 2 || kEarly) {
       if (tile < n_tiles) prefetch(tile, stage(0));
@@ -873,17 +890,19 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
       if constexpr (kEarly) {
         // no barrier after the tile: it stopped reading the buffer before
         // the barrier at which the next tile's copies were issued
-        pass_b_tile<T, L, CB, V, true, MODE>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks, [&] {
+        pass_b_tile<T, L, CB, V, true, MODE>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks, sf_sep, [&] {
           if (next < n_tiles) prefetch(next, buf);
           cp_async_commit();
         });
       } else {
-        pass_b_tile<T, L, CB, V, true, MODE>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks);
+        pass_b_tile<T, L, CB, V, true, MODE>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks, sf_sep);
         __syncthreads();  // this buffer is the prefetch target two tiles on
       }
     }
     if constexpr (MODE == kPeaks) {
-      if (ks) {  // the loop ended on a barrier: every tile's keys are in
+      if (ks) {
+        if constexpr (kEarly) __syncthreads();  // else the loop ended on one
+        // every tile's keys are in
         for (int b = threadIdx.x; b < n_bands; b += blockDim.x)
           if (ks[b]) atomicMax(pk.band_key + b, ks[b]);
       }

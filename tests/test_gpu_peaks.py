@@ -104,6 +104,30 @@ def test_peaks_equal_the_dense_output_reduced():
     plan.close()
 
 
+def test_peaks_equal_dense_for_every_pass_b_schedule():
+    # 1024-point pass-B rows: two buffers or one (the tile's 2F then in a
+    # region of its own so the next tile loads early), cp.async or TMA
+    # loads; band keys in shared memory (whole-row bands) or not.
+    t, x, plan = setup(57, n_fft=1 << 20, n=400_003)
+    tm = t.templates()
+    plan.set_split(1024)
+    for cb, vb in ((4, 0), (4, 2), (4, 4), (4, 6), (2, 2), (8, 6)):
+        plan.set_cta(1, cb, 2, vb)
+        dense = plan.compute(tm).cpu().numpy()
+        for n_bands in (2, 256, 1 << 13):
+            out = plan.compute_peaks(tm, threshold=12.0, n_bands=n_bands, capacity=1 << 18)
+            plan.sync()
+            blocks = dense.reshape(len(tm), n_bands, -1)
+            assert np.array_equal(out["band_max"].cpu().numpy(), blocks.max(axis=2)), (cb, vb, n_bands)
+            assert np.array_equal(out["band_bin"].cpu().numpy(),
+                                  blocks.argmax(axis=2) + blocks.shape[2] * np.arange(n_bands)), (cb, vb, n_bands)
+            lst = pkg.peaks_to_numpy(out)
+            ti, mi = np.nonzero(dense > 12.0)
+            assert int(out["count"].item()) == len(ti)
+            assert sorted(zip(lst["tmpl"].tolist(), lst["bin"].tolist())) == sorted(zip(ti.tolist(), mi.tolist()))
+    plan.close()
+
+
 def test_capacity_overflow_and_appending_calls():
     t, x, plan = setup(53)
     tm = t.templates()
