@@ -160,6 +160,17 @@ def ncu_traffic(kernel: str, length: int, c: int, v: int):
     return None
 
 
+def set_shape(plan, args, stream):
+    """Plan set-up for the headline workload: the FFT split and CTA shapes
+    given by --shape, else the autotuner's choice."""
+    if args.shape:
+        n1_, ca, va, cb, vb = (int(v) for v in args.shape.split(","))
+        plan.set_split(n1_)
+        plan.set_cta(ca, cb, va, vb)
+    else:
+        plan.autotune(stream)
+
+
 def reduce_max(value: float, world: int, device=None) -> float:
     """The slowest rank's number (whole-job time = max over replicas)."""
     if world <= 1:
@@ -305,12 +316,7 @@ def run_ours(args, rank, world, local_rank):
     for X in range(len(t.detectors)):
         plan.set_data(X, xs[X], t.sigmas[X])
     plan.set_streams(args.streams)
-    if args.shape:                      # plan set-up: FFT split and CTA shapes
-        n1_, ca, va, cb, vb = (int(v) for v in args.shape.split(","))
-        plan.set_split(n1_)
-        plan.set_cta(ca, cb, va, vb)
-    else:
-        plan.autotune(stream)
+    set_shape(plan, args, stream)
     out = torch.empty((chunk, n_fft), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > L2
     chunks = [tm[i:i + chunk] for i in range(0, n_tmpl, chunk)]
@@ -799,7 +805,7 @@ def e2e(t, xs, tm, chunk, dev, stream, args):
     plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
     for X in range(len(t.detectors)):
         plan.set_data(X, hx[X].numpy(), t.sigmas[X])
-    plan.autotune(stream)               # served from the in-process cache
+    set_shape(plan, args, stream)       # the autotuner's choice from its in-process cache
     dbuf = [torch.empty((chunk, n_fft), dtype=torch.float32, device=dev) for _ in range(2)]
     hbuf = [torch.empty((chunk, n_fft), dtype=torch.float32, pin_memory=True) for _ in range(2)]
     copy = torch.cuda.Stream(dev)
@@ -856,7 +862,7 @@ def e2e_peaks(t, xs, tm, chunk, dev, stream, args):
     plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
     for X in range(len(t.detectors)):
         plan.set_data(X, hx[X].numpy(), t.sigmas[X])
-    plan.autotune(stream)
+    set_shape(plan, args, stream)
     chunks = [(i, tm[i:i + chunk]) for i in range(0, len(tm), chunk)]
     outs = [{"count": torch.zeros(1, dtype=torch.int64, device=dev),
              "peaks": torch.empty((PEAK_CAPACITY, 4), dtype=torch.int32, device=dev)} for _ in range(2)]
