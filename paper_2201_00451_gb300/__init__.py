@@ -442,9 +442,16 @@ class FstatPlan:
         return a.value, b.value
 
     def set_residency(self, ra: int, rb: int):
+        """fstat_set_residency: at most ra (pass A) / rb (pass B) persistent
+        CTAs per SM, 0 = every CTA that fits."""
         _check(self._lib.fstat_set_residency(self._p, int(ra), int(rb)), "fstat_set_residency")
 
     def set_cta(self, ca: int, cb: int, va: int = 0, vb: int = 0):
+        """fstat_set_cta: columns per CTA of pass A (ca), rows per CTA of pass
+        B (cb), 0 = the length's default; schedules va (0..3 or 10) and vb
+        (0..7): bit 0 radix-8 first, bit 1 one buffer (register-capped for
+        two CTAs per SM), bit 2 pass-B tiles by TMA, bit 3 pass A three CTAs
+        per SM."""
         _check(self._lib.fstat_set_cta(self._p, int(ca), int(va), int(cb), int(vb)), "fstat_set_cta")
 
     def set_streams(self, n: int):
