@@ -272,16 +272,17 @@ int fstat_set_split(fstat_plan* plan, int64_t n1);
 /* Launch shapes of the two FFT passes: columns per CTA of pass A (ca),
  * rows per CTA of pass B (cb), 0 = default for the length; schedule va /
  * vb: bit 0 = radix-8 first (lengths >= 1024, else radix-16 first), bit 1 =
- * one shared-memory buffer instead of two (no prefetch, half the shared
- * memory; radix-16 CTAs of up to 256 threads are then register-capped so
- * that two share an SM); va only: bit 3 (with bit 1, radix-16) = three
- * CTAs per SM; vb only: bit 2 = pass B tile loads by the tensor-memory-
- * access engine (FP32, rows of 1024 points or more; a load that does not
- * complete within a bounded wait ends the kernel, and fstat_sync() then
- * returns FSTAT_ERR_TIMEOUT).  va 0..3 or 10, vb 0..7.  A shape that is
- * not compiled for the current split makes fstat_compute return
- * FSTAT_ERR_CUDA.  fstat_get_cta reports the shapes
- * in effect (a default as its value for the current split). */
+ * one shared-memory buffer instead of two (half the shared memory; the
+ * next tile's copies start once the last FFT pass has read the buffer;
+ * radix-16 CTAs of up to 256 threads are register-capped so that two share
+ * an SM); va only: bit 3 (with bit 1, radix-16) = three CTAs per SM; vb
+ * only: bit 2 = pass B tile loads by the tensor-memory-access engine
+ * (FP32, rows of 1024 points or more; a load that does not complete within
+ * a bounded wait ends the kernel, and fstat_sync() then returns
+ * FSTAT_ERR_TIMEOUT).  va 0..3 or 10, vb 0..7.  A shape that is not
+ * compiled for the current split makes fstat_compute return
+ * FSTAT_ERR_CUDA.  fstat_get_cta reports the shapes in effect (a default
+ * as its value for the current split). */
 int fstat_get_cta(const fstat_plan* plan, int* ca, int* va, int* cb, int* vb);
 int fstat_set_cta(fstat_plan* plan, int ca, int va, int cb, int vb);
 
