@@ -180,10 +180,13 @@ __global__ void k_cand_consts(const fstat_candidate* __restrict__ cand, int n, d
 
 // accumulated quantities (kAcc): 0-1 Fa, 2-3 Fb, 4-7 dFa,dFb/df, 8-11 d/df1dot,
 // 12-15 d/dalpha, 16-19 d/ddelta, 20-22 A,B,C, 23-25 dA,dB,dC/dalpha, 26-28 d/ddelta
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, 3)
 k_partial(Geo g, SampleTabs tab, const CandConst* __restrict__ cc, int n_cand, int n_chunks,
           double* __restrict__ partial) {
   __shared__ CandConst sc[kWarps];
+  // second-level sums of every lane, in shared memory so that the registers
+  // hold the candidate's constants instead (same FP32 arithmetic)
+  __shared__ float s_outer[kWarps][kAcc][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cand = blockIdx.x * kWarps + warp;
   const int chunk = blockIdx.y;
@@ -199,9 +202,10 @@ k_partial(Geo g, SampleTabs tab, const CandConst* __restrict__ cc, int n_cand, i
   const df c0 = df_from(g.t0 - g.t_ref);
   const float two_pi = 6.28318530717958647692f;
 
-  float outer[kAcc], inner[kAcc];
+  float inner[kAcc];
+  float* outer = &s_outer[warp][0][lane];  // element q at outer[32 q]
 #pragma unroll
-  for (int q = 0; q < kAcc; ++q) outer[q] = 0.f;
+  for (int q = 0; q < kAcc; ++q) outer[32 * q] = 0.f;
   int cnt = 0;
 #pragma unroll
   for (int q = 0; q < kAcc; ++q) inner[q] = 0.f;
@@ -276,14 +280,14 @@ k_partial(Geo g, SampleTabs tab, const CandConst* __restrict__ cc, int n_cand, i
     inner[28] += w * (ad * b + a * bd);
     if (++cnt == kInner) {
 #pragma unroll
-      for (int q = 0; q < kAcc; ++q) { outer[q] += inner[q]; inner[q] = 0.f; }
+      for (int q = 0; q < kAcc; ++q) { outer[32 * q] += inner[q]; inner[q] = 0.f; }
       cnt = 0;
     }
   }
   double* dst = partial + ((int64_t)cand * n_chunks + chunk) * kAcc;
 #pragma unroll
   for (int q = 0; q < kAcc; ++q) {
-    double v = (double)outer[q] + (double)inner[q];
+    double v = (double)outer[32 * q] + (double)inner[q];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) dst[q] = v;
   }
