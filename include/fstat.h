@@ -34,6 +34,14 @@
 extern "C" {
 #endif
 
+/* The library is built with hidden symbol visibility; only the entry points
+ * declared here are exported (so that two builds loaded into one process,
+ * such as a test's deliberately degraded variant, keep separate internal
+ * state). */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 #define FSTAT_MAX_DET 4
 
 enum {
@@ -44,7 +52,9 @@ enum {
   FSTAT_ERR_DEGENERATE = -4,  /* D = AB - C^2 <= 1e-12 AB for a sky position  */
   FSTAT_ERR_NONFINITE = -5,   /* NaN or Inf in the input series               */
   FSTAT_ERR_NOT_READY = -6,   /* compute before every detector has data       */
-  FSTAT_ERR_UNSUPPORTED = -7, /* size outside the compiled FFT range          */
+  FSTAT_ERR_UNSUPPORTED = -7, /* size outside the compiled FFT range, or a
+                                 spindown phase excursion over the data
+                                 above 2^20 cycles                          */
   FSTAT_ERR_TIMEOUT = -8      /* a kernel's bounded wait for its own copies ran out */
 };
 
@@ -92,7 +102,8 @@ typedef struct {
   int64_t n_samples;  /* N, 1..2^24-1                                        */
   double f_het;       /* heterodyne frequency f_h                            */
   int64_t n_fft;      /* zero-padded FFT length: power of two, 2^10..2^24, >= N */
-  double t_ref;       /* spindown reference time; NaN -> t0 + floor(N/2) dt  */
+  double t_ref;       /* spindown reference time (finite, anywhere); NaN ->
+                         t0 + floor(N/2) dt                                 */
   fstat_ephemeris ephem;
 } fstat_plan_desc;
 
@@ -111,7 +122,12 @@ typedef struct fstat_plan fstat_plan;
 
 /* Create a plan on the current CUDA device.  Allocates all device buffers
  * the plan needs (x_h copies, per-sky resampled series, FFT workspace).
- * *out receives the plan; destroy it with fstat_plan_destroy.
+ * *out receives the plan; destroy it with fstat_plan_destroy.  If the
+ * environment variable FSTAT_DEVICE_BYTES_CAP holds a byte count when the
+ * plan is created, the device memory the plan allocates over its life
+ * (here and in later calls that grow its buffers) is capped there: a request
+ * past the cap fails with OOM, as on an exhausted device, leaving the plan
+ * (or, here, nothing) in a usable state.
  * Errors: INVALID_ARG (NULL pointers, fields out of range), UNSUPPORTED
  * (n_fft outside 2^10..2^24), OOM, CUDA. */
 int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out);
@@ -155,8 +171,12 @@ int fstat_export_data(fstat_plan* plan, int det, void* out, void* stream);
  * row-major [template][bin] in ascending frequency.  Templates are grouped
  * by sky position internally; per-sky work (steps iii-v) runs once per group
  * and is reused across calls while the sky position does not change.
- * Errors: INVALID_ARG, NOT_READY (a detector has no data), CUDA; kernel-side
- * DEGENERATE is reported by fstat_sync. */
+ * The spindown phase is expanded about the data sample nearest t_ref
+ * (clamped into the data), so t_ref may lie anywhere; a template whose
+ * spindown phase excursion over the data, |f1dot| tau^2 + |f2dot| |tau|^3/3
+ * with tau the largest |t_b - t_ref|, reaches 2^20 cycles is rejected.
+ * Errors: INVALID_ARG, NOT_READY (a detector has no data), UNSUPPORTED
+ * (that excursion), CUDA; kernel-side DEGENERATE is reported by fstat_sync. */
 int fstat_compute(fstat_plan* plan, const fstat_template* tmpl, int64_t n_tmpl, float* twoF,
                   void* stream);
 
@@ -299,6 +319,15 @@ int fstat_get_residency(const fstat_plan* plan, int* ra, int* rb);
  * overlap.  Synchronises. */
 int fstat_set_streams(fstat_plan* plan, int n);
 
+/* Polls of the first wait for each of pass B's bulk tensor copies (the
+ * TMA schedules, vb bit 2): a kernel that waits longer records
+ * FSTAT_ERR_TIMEOUT (returned by fstat_sync), lets its copies in flight land
+ * under the full default limit, and returns.  polls < 0 restores the default
+ * (2^22 polls); 0 makes every first wait give up at once, which tests of the
+ * timeout path use.  Takes effect for work enqueued after the call.
+ * Errors: INVALID_ARG (NULL plan). */
+int fstat_set_wait_limit(fstat_plan* plan, int polls);
+
 /* Autotuner: times every compiled (split, ca, va, cb, vb) for this plan's n_fft on
  * the current data with CUDA events on `stream` and keeps the fastest.
  * Results are cached per (GPU name, n_samples, n_fft, precision, n_det) in
@@ -312,14 +341,19 @@ int fstat_autotune(fstat_plan* plan, void* stream);
  * not call cudaMalloc (a plug-in inside an application whose memory pool
  * owns the device memory, or a pipeline that must not allocate after
  * start-up).  Its scratch memory is a fixed file-scope device array of
- * 8.1 MB, reserved on every GPU that loads the library until exit.
+ * 8.1 MB.  CUDA loads the library's modules lazily, so the array is
+ * reserved on a device by the first call there (and held until exit): a
+ * caller whose pool claims the rest of the device memory makes that first
+ * call at start-up.
  *   g_pairs   DEVICE, n_samples float4 (Ga.re, Ga.im, Gb.re, Gb.im) in SSB
  *             sample order j (the detector-summed, antenna-weighted series
  *             G_a, G_b; fstat_export_sky returns them), 16-byte aligned
  *   n_samples 1..n_fft;  n_fft: power of two, 2^10..2^18 (larger sizes
  *             return FSTAT_ERR_UNSUPPORTED)
  *   dt, tau0  sample spacing; SSB time of sample 0 minus the spindown
- *             reference time, so tau_j = tau0 + j dt
+ *             reference time, so tau_j = tau0 + j dt (finite; the spindown
+ *             phase excursion |f1dot| tau^2 + |f2dot| |tau|^3 / 3 over the
+ *             data must stay below 2^20 cycles, else UNSUPPORTED)
  *   A, B, C   antenna-pattern integrals of the series (D = AB - C^2 > 0)
  *   twoF      DEVICE output, n_fft floats, ascending frequency
  * Every call shares the scratch array, which keeps the previous call's
@@ -358,8 +392,26 @@ int fstat_batch_launch(fstat_batch* batch, void* stream);
 int fstat_batch_nodes(const fstat_batch* batch, int64_t* nodes);
 void fstat_batch_destroy(fstat_batch* batch);
 
+/* Machine peak for roofline figures (not part of the F-statistic): the
+ * fused multiply-add rate of the current device's CUDA cores in FP32
+ * (precision = FSTAT_MIXED) or FP64 (FSTAT_FP64), from a kernel of
+ * independent FMA chains on every SM, `iters` FMAs per chain, timed with
+ * CUDA events on `stream` after one warm-up launch.  *tflops = 2 flops per
+ * FMA / seconds / 1e12; *ms (may be NULL) = the timed launch.  Synchronises.
+ * Errors: INVALID_ARG, CUDA. */
+int fstat_probe_fma(int precision, int64_t iters, double* tflops, double* ms, void* stream);
+
+/* Kernel launches this plan has enqueued since it was created (every
+ * kernel of the per-sky work, the spindown coefficients and the FFT
+ * passes), for launch accounting.  Errors: INVALID_ARG. */
+int fstat_launch_count(const fstat_plan* plan, int64_t* launches);
+
 void fstat_plan_destroy(fstat_plan* plan);
 const char* fstat_strerror(int code);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
 
 #ifdef __cplusplus
 }

@@ -47,7 +47,8 @@ EXPORTS = (
     "fstat_grad", "fstat_batch_create", "fstat_batch_add", "fstat_batch_instantiate",
     "fstat_batch_launch", "fstat_batch_nodes", "fstat_batch_destroy", "fstat_set_streams",
     "fstat_compute_peaks", "fstat_semicoherent", "fstat_set_residency", "fstat_get_residency",
-    "fstat_set_sfts", "fstat_export_data", "fstat_reduce_peaks",
+    "fstat_set_sfts", "fstat_export_data", "fstat_reduce_peaks", "fstat_set_wait_limit",
+    "fstat_probe_fma", "fstat_launch_count",
 )
 
 
@@ -108,6 +109,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     global _lib
     if _lib is not None:
         return _lib
+    _lib = open_library(path)
+    return _lib
+
+
+def open_library(path: str) -> ctypes.CDLL:
+    """Open a build of the library at ``path`` (not cached; ``load`` keeps
+    the package's own) with its signatures declared.  Plans take it through
+    ``FstatPlan(desc, lib=...)``."""
     if not os.path.exists(path):
         raise FstatLibraryMissing(
             f"{path} is not built; run paper_2201_00451_gb300.build.build() (needs nvcc)")
@@ -147,12 +156,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "fstat_export_data": (i32, [P, i32, P, P]),
         "fstat_reduce_peaks": (i32, [P, P, i64, ctypes.POINTER(PeakOut), P]),
         "fstat_get_residency": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "fstat_set_wait_limit": (i32, [P, i32]),
+        "fstat_probe_fma": (i32, [i32, i64, ctypes.POINTER(dbl), ctypes.POINTER(dbl), P]),
+        "fstat_launch_count": (i32, [P, ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _lib = lib
     return lib
 
 
@@ -213,8 +224,8 @@ def as_templates(templates) -> np.ndarray:
 class FstatPlan:
     """A plan: sample grid, detectors, FFT length, precision (fstat_plan_*)."""
 
-    def __init__(self, desc: PlanDesc):
-        self._lib = load()
+    def __init__(self, desc: PlanDesc, lib=None):
+        self._lib = lib if lib is not None else load()
         self._p = ctypes.c_void_p()
         _check(self._lib.fstat_plan_create(ctypes.byref(desc), ctypes.byref(self._p)), "fstat_plan_create")
         self.desc = desc
@@ -222,17 +233,18 @@ class FstatPlan:
         self.n_samples = int(desc.n_samples)
 
     @classmethod
-    def from_target(cls, target, precision=MIXED, dterms=None, interp=None):
+    def from_target(cls, target, precision=MIXED, dterms=None, interp=None, lib=None):
         """Plan for an object exposing the workload fields (detectors, t0, dt,
         n_samples, f_het, n_fft, dterms, t_ref, ephemeris; interp optional).
-        ``dterms`` / ``interp`` override the target's."""
+        ``dterms`` / ``interp`` override the target's; ``lib``: a library
+        from ``open_library`` instead of the package's own."""
         if interp is None:
             interp = getattr(target, "interp", INTERP_TAPERED)
         return cls(make_desc(detectors=target.detectors, t0=target.t0, dt=target.dt,
                              n_samples=target.n_samples, f_het=target.f_het, n_fft=target.n_fft,
                              dterms=target.dterms if dterms is None else dterms,
                              precision=precision, t_ref=target.t_ref, ephemeris=target.ephemeris,
-                             interp=interp))
+                             interp=interp), lib=lib)
 
     # -- lifetime
     def close(self):
@@ -458,9 +470,29 @@ class FstatPlan:
         """fstat_set_streams: templates rotate over n streams (1..8)."""
         _check(self._lib.fstat_set_streams(self._p, int(n)), "fstat_set_streams")
 
+    @property
+    def launches(self) -> int:
+        """fstat_launch_count: kernel launches enqueued since creation."""
+        n = ctypes.c_int64()
+        _check(self._lib.fstat_launch_count(self._p, ctypes.byref(n)), "fstat_launch_count")
+        return n.value
+
+    def set_wait_limit(self, polls: int):
+        """fstat_set_wait_limit: polls of pass B's first bulk-copy wait per
+        tile (< 0 restores the default)."""
+        _check(self._lib.fstat_set_wait_limit(self._p, int(polls)), "fstat_set_wait_limit")
+
     def autotune(self, stream=None):
         """fstat_autotune: pick the fastest FFT split and CTA shapes."""
         _check(self._lib.fstat_autotune(self._p, _stream_handle(stream)), "fstat_autotune")
+
+
+def probe_fma(precision=MIXED, iters: int = 1 << 16, stream=None):
+    """fstat_probe_fma: measured FMA rate of the CUDA cores, (TFLOP/s, ms)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().fstat_probe_fma(int(precision), int(iters), ctypes.byref(tf), ctypes.byref(ms),
+                                  _stream_handle(stream)), "fstat_probe_fma")
+    return tf.value, ms.value
 
 
 def semicoherent(plans, templates, t_ref: float, out=None, stream=None):

@@ -23,8 +23,11 @@ LIB = os.path.join(HERE, "libfstat.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no floating-point contraction, so host arithmetic (template
 # shifts, validation) rounds the same on x86-64 and aarch64
+# host code: hidden visibility, so only the fstat_* entry points (declared
+# default-visible in fstat.h) are exported and template statics stay private
+# to each build of the library
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-              "--expt-relaxed-constexpr", "-I" + INCLUDE] + ARCH
+              "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr", "-I" + INCLUDE] + ARCH
 
 
 def _nvcc() -> str:
@@ -86,6 +89,35 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, LIB)
     return LIB
+
+
+def build_variant(tag: str, defines, units=("sky.cu",), verbose: bool = False) -> str:
+    """A second build of the library in which ``units`` are compiled with
+    the extra preprocessor ``defines`` (the other objects are the regular
+    build's): _build/libfstat_<tag>.so.  ``units``: file names under csrc/.  Used by tests that need a
+    deliberately degraded library (the precision negative control)."""
+    build(verbose=verbose)
+    nvcc = _nvcc()
+    out_dir = os.path.join(BUILD, tag)
+    os.makedirs(out_dir, exist_ok=True)
+    lib = os.path.join(BUILD, f"libfstat_{tag}.so")
+    flags = [f"-D{d}" for d in defines]
+    objs = []
+    for src in sources():
+        name = os.path.basename(src)
+        if name in units:
+            obj = os.path.join(out_dir, name + ".o")
+            r = subprocess.run([nvcc, *NVCC_FLAGS, *flags, "-c", src, "-o", obj], capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"nvcc failed on {name} ({tag}):\n" + r.stdout + r.stderr)
+        else:
+            obj = os.path.join(BUILD, name + ".o")
+        objs.append(obj)
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", lib, *objs,
+                        "-Xlinker", "-rpath,/usr/local/cuda/lib64"], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
+    return lib
 
 
 if __name__ == "__main__":

@@ -339,7 +339,7 @@ cudaError_t launch_grad_tables(const Geo& g, const void* const* xh, const int* d
   tab.d1 = (float2*)p; p += 8 * tot;
   tab.x = (float2*)p;
   int blocks = (int)((g.n + 255) / 256);
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > device_sm_count() * 32) blocks = device_sm_count() * 32;
   for (int X = 0; X < g.n_det; ++X)
     adj::k_tables<<<blocks, 256, 0, st>>>(g, X, xh[X], dtype[X], tab);
   return cudaGetLastError();

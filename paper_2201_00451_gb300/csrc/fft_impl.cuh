@@ -172,8 +172,8 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (int i = 0; i < kWaitLimit; ++i)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int limit = kWaitLimit) {
+  for (int i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -816,7 +816,9 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
           if (it > 0) issue(tile, 0);  // the previous tile released the only stage
         }
       }
-      const bool ok = mbar_wait(&s_bar[b], waited[b] & 1u);
+      // the plan may shorten this first wait (tests of the timeout path); the
+      // drain below always keeps the full limit
+      const bool ok = mbar_wait(&s_bar[b], waited[b] & 1u, pk.wait_set ? pk.wait_limit : kWaitLimit);
       if (ok) ++waited[b];
       all_ok = __syncthreads_and(ok) != 0;
       if (!all_ok) break;

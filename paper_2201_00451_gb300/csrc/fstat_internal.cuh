@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "../../include/fstat.h"
@@ -39,6 +40,48 @@ struct TmplCoef {
   int J;
   int pad_;
 };
+
+// Spindown phase polynomial of one template (eqs. Fa, Fb: Phi_s =
+// 2 pi (f1dot tau^2/2 + f2dot tau^3/6)) for samples j with tau_j = (j - jr) dt,
+// expanded in s = j - J.  J is the integer nearest jr clamped into the data
+// [0, n - 1], so |s| < n < 2^24 stays exact in FP32 wherever the reference
+// time lies; p0, a phase common to every sample that cancels in 2F, is
+// reduced mod 1.
+__host__ __device__ inline TmplCoef spin_coef(double jr, int64_t n, double dt, double f1dot, double f2dot) {
+  double J = rint(jr);
+  if (!(J >= 0.0)) J = 0.0;
+  if (J > (double)(n - 1)) J = (double)(n - 1);
+  const double e = jr - J;  // tau_j = (s - e) dt
+  const double c2 = f1dot * dt * dt / 2.0;
+  const double c3 = f2dot * dt * dt * dt / 6.0;
+  TmplCoef c;
+  c.p[3] = c3;
+  c.p[2] = c2 - 3.0 * c3 * e;
+  c.p[1] = -2.0 * c2 * e + 3.0 * c3 * e * e;
+  const double p0 = c2 * e * e - c3 * e * e * e;
+  c.p[0] = p0 - rint(p0);
+  for (int q = 0; q < 4; ++q) {
+    const float h = (float)c.p[q];
+    c.hi[q] = h;
+    c.lo[q] = (float)(c.p[q] - (double)h);
+  }
+  c.J = (int)J;
+  c.pad_ = 0;
+  return c;
+}
+
+// Largest spindown phase excursion over the data (cycles) that the FP32
+// path's double-float evaluation reduces mod 1 exactly (its reduced phase
+// then stays within [-0.57, 0.57] cycles).  tmax bounds |tau| over the data
+// samples; twice max |Phi_s| / 2 pi bounds the excursion.
+constexpr double kMaxSpinCycles = 1048576.0;  // 2^20
+inline bool spin_in_range(double tmax, double f1dot, double f2dot) {
+  const double b = fabs(f1dot) * tmax * tmax + fabs(f2dot) * tmax * tmax * tmax / 3.0;
+  return b < kMaxSpinCycles;
+}
+
+// Streaming multiprocessors of the current device (host; cached per device).
+int device_sm_count();
 
 // One entry of the sky-independent timing table (sky.cu): cos, sin of the
 // orbital phase and of the sidereal rotation angle.
@@ -124,7 +167,7 @@ void launch_sky(const Geo& g, int precision, double alpha, double delta, const v
 // kernel that fills them (FP64 sincos, once per plan).
 int time_table_entries(double t_lo, double t_hi, double h);
 cudaError_t launch_time_table(const Geo& g, TimeTab* tab, cudaStream_t st);
-void launch_tmpl_coef(const SkyConst* sky, double dt, const fstat_template* tmpl,
+void launch_tmpl_coef(const SkyConst* sky, double dt, int64_t n, const fstat_template* tmpl,
                       const int* order, int first, int count, TmplCoef* out, cudaStream_t st);
 void launch_check_finite(const void* x, int dtype, int64_t n, int* err, cudaStream_t st);
 // Gradient (adjoint.cu): per-plan sample tables and per-call scratch.
@@ -160,6 +203,9 @@ struct PeakArgs {
   int log2_band;                 // log2(bins per band)
   int shift;                     // accumulate: bin m adds to bin m - shift
   int* err;                      // where a pass records FSTAT_ERR_TIMEOUT, or nullptr
+  int wait_limit;                // polls of a tile's first bulk-copy wait (<= 0 with
+                                 // wait_set: give up at once; unset: the default)
+  int wait_set;
 };
 
 // Band key: order-preserving image of the float 2F in the high word, the
@@ -180,15 +226,18 @@ cudaError_t launch_pass_a_f32(int log2_n2, int ca, int va, const void* G, int64_
                               void* Z, cudaStream_t st, int res = 0);
 // pk == nullptr: write 2F to out[n_fft]; otherwise reduce it as pk says.
 // err: where a pass records a timed-out wait (FSTAT_ERR_TIMEOUT), or nullptr
+// wait_limit >= 0: polls of each tile's first bulk-copy wait (timeout tests)
 cudaError_t launch_pass_b_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                               const SkyConst* sky, float* out, cudaStream_t st,
-                              const PeakArgs* pk = nullptr, int res = 0, int* err = nullptr);
+                              const PeakArgs* pk = nullptr, int res = 0, int* err = nullptr,
+                              int wait_limit = -1);
 cudaError_t launch_pass_a_f64(int log2_n2, int ca, int va, const void* G, int64_t lc, int64_t n, int n1,
                               const void* twA, const void* hi, const void* lo, int h, const TmplCoef* coef,
                               void* Z, cudaStream_t st, int res = 0);
 cudaError_t launch_pass_b_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                               const SkyConst* sky, float* out, cudaStream_t st,
-                              const PeakArgs* pk = nullptr, int res = 0, int* err = nullptr);
+                              const PeakArgs* pk = nullptr, int res = 0, int* err = nullptr,
+                              int wait_limit = -1);
 cudaError_t launch_pass_b_peak_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                                    const SkyConst* sky, const PeakArgs& pk, cudaStream_t st, int res = 0);
 cudaError_t launch_pass_b_peak_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
@@ -196,10 +245,15 @@ cudaError_t launch_pass_b_peak_f64(int log2_n1, int cb, int vb, const void* Z, i
 // Accumulate mode: out[m - shift] += 2F[m] for 0 <= m - shift < n_fft.
 cudaError_t launch_pass_b_acc_f32(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                                   const SkyConst* sky, float* out, int shift, cudaStream_t st, int res = 0,
-                                  int* err = nullptr);
+                                  int* err = nullptr, int wait_limit = -1);
 cudaError_t launch_pass_b_acc_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                                   const SkyConst* sky, float* out, int shift, cudaStream_t st, int res = 0,
-                                  int* err = nullptr);
+                                  int* err = nullptr, int wait_limit = -1);
+// PeakArgs' wait fields from a plan's setting (< 0: the default limit)
+inline void set_wait(PeakArgs& a, int wait_limit) {
+  a.wait_set = wait_limit >= 0;
+  a.wait_limit = wait_limit >= 0 ? wait_limit : 0;
+}
 // Band keys of n rows x n_bands -> maximum 2F and its bin (band_bin may be null).
 cudaError_t launch_band_decode(const unsigned long long* keys, int64_t count, float* band_max,
                                int32_t* band_bin, cudaStream_t st);

@@ -6,8 +6,12 @@
 // outside allocations, and a low-latency pipeline that must not allocate
 // after start-up because cudaMalloc can synchronise the device and has no
 // latency bound.  This entry point keeps its working memory in file-scope
-// __device__ arrays of fixed size, reserved when the library is loaded
-// (every GPU that loads libfstat holds them until the process exits).
+// __device__ arrays of fixed size (8.1 MB).  With CUDA's lazy module loading
+// (the default since CUDA 12.2) the arrays are reserved on a device when
+// this file's module is first used there, i.e. by the first call on that
+// device; from then on the device holds them until the process exits.  A
+// caller whose pool takes the rest of the device memory should make that
+// first call at start-up, before the pool claims the memory.
 //
 // It runs the same FFT pass kernels as fstat_compute (spindown phase +
 // column FFTs, then row FFTs + eq. Fstat); only the scratch memory differs.
@@ -70,10 +74,9 @@ int device_ptrs(DevPtrs* out) {
 }
 
 // Per-call constants: 2F weights from A, B, C and the spindown polynomial
-// phi(s) = p0 + p1 s + p2 s^2 + p3 s^3 (cycles), s = j - J, for
-// tau = tau0 + j dt = (j - j_ref) dt with j_ref = -tau0 / dt.
-__global__ void k_noalloc_setup(double A, double B, double C, double tau0, double dt, double f1dot,
-                                double f2dot) {
+// in s = j - J for tau_j = tau0 + j dt = (j - j_ref) dt, j_ref = -tau0 / dt.
+__global__ void k_noalloc_setup(double A, double B, double C, double tau0, double dt, int64_t n,
+                                double f1dot, double f2dot) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double D = A * B - C * C;
   g_scratch_sky.A = A;
@@ -86,24 +89,7 @@ __global__ void k_noalloc_setup(double A, double B, double C, double tau0, doubl
   g_scratch_sky.kAf = (float)g_scratch_sky.kA;
   g_scratch_sky.kBf = (float)g_scratch_sky.kB;
   g_scratch_sky.kCf = (float)g_scratch_sky.kC;
-  double jr = -tau0 / dt;
-  double J = rint(jr);
-  double e = jr - J;
-  double c2 = f1dot * dt * dt / 2.0;
-  double c3 = f2dot * dt * dt * dt / 6.0;
-  TmplCoef c;
-  c.p[3] = c3;
-  c.p[2] = c2 - 3.0 * c3 * e;
-  c.p[1] = -2.0 * c2 * e + 3.0 * c3 * e * e;
-  c.p[0] = c2 * e * e - c3 * e * e * e;
-  for (int q = 0; q < 4; ++q) {
-    float h = (float)c.p[q];
-    c.hi[q] = h;
-    c.lo[q] = (float)(c.p[q] - (double)h);
-  }
-  c.J = (int)J;
-  c.pad_ = 0;
-  g_scratch_coef = c;
+  g_scratch_coef = spin_coef(-tau0 / dt, n, dt, f1dot, f2dot);
 }
 
 // natural order j -> column-major [(j mod n1) * lc + j / n1]
@@ -132,6 +118,10 @@ extern "C" int fstat_twoF_noalloc(const void* g_pairs, int64_t n_samples, int64_
   if (n_samples > n_fft) return FSTAT_ERR_INVALID_ARG;
   double D = A * B - C * C;
   if (!(D > 1e-12 * A * B) || !(A > 0.0) || !(B > 0.0)) return FSTAT_ERR_DEGENERATE;
+  // spindown phase excursion over the data within what the phase evaluation
+  // reduces exactly (this also bounds |tau0|)
+  const double tmax = fmax(fabs(tau0), fabs(tau0 + (double)(n_samples - 1) * dt)) + dt;
+  if (!spin_in_range(tmax, f1dot, f2dot)) return FSTAT_ERR_UNSUPPORTED;
 
   DevPtrs p;
   int rc = device_ptrs(&p);
@@ -141,9 +131,9 @@ extern "C" int fstat_twoF_noalloc(const void* g_pairs, int64_t n_samples, int64_
   const int n1 = 1 << log2n1, n2 = 1 << log2n2;
   const int64_t lc = (n_samples + n1 - 1) / n1;
 
-  k_noalloc_setup<<<1, 32, 0, st>>>(A, B, C, tau0, dt, f1dot, f2dot);
+  k_noalloc_setup<<<1, 32, 0, st>>>(A, B, C, tau0, dt, n_samples, f1dot, f2dot);
   int blocks = (int)((n_samples + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
   k_noalloc_columns<<<blocks, 256, 0, st>>>((const float4*)g_pairs, n_samples, n1, lc, p.G);
   if (cudaGetLastError() != cudaSuccess) return FSTAT_ERR_CUDA;
   cudaError_t e = build_twiddles(FSTAT_MIXED, log2n1, log2n2, p.tw, st);

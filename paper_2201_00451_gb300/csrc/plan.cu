@@ -103,6 +103,12 @@ struct fstat_plan {
   // peaks mode: band keys [templates of the call][n_bands]
   unsigned long long* keys = nullptr;
   int64_t keys_cap = 0;
+  // device memory this plan has allocated over its life, and the cap on it
+  // (0 = none) read at creation from FSTAT_DEVICE_BYTES_CAP
+  size_t alloc_bytes = 0, alloc_cap = 0;
+  // polls of the first wait for a pass-B tile's bulk copies (< 0: default)
+  int wait_limit = -1;
+  int64_t n_launches = 0;  // kernel launches enqueued (fstat_launch_count)
 };
 
 namespace {
@@ -118,6 +124,19 @@ int cuda_status(cudaError_t e) {
     cudaError_t e_ = (call);                     \
     if (e_ != cudaSuccess) return cuda_status(e_); \
   } while (0)
+
+// Plan-owned device allocation, counted against the plan's cap: a cap that
+// the request would pass fails like an exhausted device (FSTAT_ERR_OOM).
+template <typename Ptr>
+cudaError_t palloc(fstat_plan* p, Ptr** ptr, size_t bytes) {
+  if (p->alloc_cap && p->alloc_bytes + bytes > p->alloc_cap) return cudaErrorMemoryAllocation;
+  void* v = nullptr;
+  const cudaError_t e = cudaMalloc(&v, bytes);
+  if (e != cudaSuccess) return e;
+  *ptr = static_cast<Ptr*>(v);
+  p->alloc_bytes += bytes;
+  return cudaSuccess;
+}
 
 int ilog2_exact(int64_t v) {
   if (v <= 0 || (v & (v - 1))) return -1;
@@ -174,9 +193,9 @@ int ensure_capacity(fstat_plan* p, int64_t n) {
   if (p->h_order) cudaFreeHost(p->h_order);
   p->d_tmpl = nullptr; p->d_order = nullptr; p->d_coef = nullptr; p->h_tmpl = nullptr; p->h_order = nullptr;
   p->cap = 0;
-  CK(cudaMalloc(&p->d_tmpl, c * sizeof(fstat_template)));
-  CK(cudaMalloc(&p->d_order, c * sizeof(int)));
-  CK(cudaMalloc(&p->d_coef, c * sizeof(TmplCoef)));
+  CK(palloc(p, &p->d_tmpl, c * sizeof(fstat_template)));
+  CK(palloc(p, &p->d_order, c * sizeof(int)));
+  CK(palloc(p, &p->d_coef, c * sizeof(TmplCoef)));
   CK(cudaMallocHost(&p->h_tmpl, c * sizeof(fstat_template)));
   CK(cudaMallocHost(&p->h_order, c * sizeof(int)));
   p->cap = c;
@@ -199,6 +218,7 @@ int run_sky(fstat_plan* p, double alpha, double delta, cudaStream_t st) {
   launch_sky(p->geo, p->d.precision, alpha, delta, xh, p->dtype, p->z, p->G, (int)p->n1, p->lc,
              p->partials, p->nblk, p->sky, p->d_err, st);
   CK(cudaGetLastError());
+  p->n_launches += 4 + p->d.n_det;  // setup, delay table, step iii per detector, resampling, finalize
   if (p->prof) { cudaEventRecord(e.b, st); p->ev[2].push_back(e); p->launches[2]++; }
   p->sky_valid = true;
   p->sky_alpha = alpha;
@@ -229,6 +249,7 @@ cudaError_t launch_a(fstat_plan* p, int ca, int va, const TmplCoef* coef, cudaSt
   const TwiddleTables& t = p->tt;
   if (!Z) Z = p->Z;
   if (res < 0) res = p->ra;
+  ++p->n_launches;
   return p->d.precision == FSTAT_FP64
       ? launch_pass_a_f64(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, Z, st, res)
       : launch_pass_a_f32(p->log2n2, ca, va, p->G, p->lc, p->d.n_samples, (int)p->n1, t.a, t.hi, t.lo, t.h, coef, Z, st, res);
@@ -239,16 +260,20 @@ cudaError_t launch_b(fstat_plan* p, int cb, int vb, float* out, cudaStream_t st,
   const TwiddleTables& t = p->tt;
   if (!Z) Z = p->Z;
   if (res < 0) res = p->rb;
+  ++p->n_launches;
   return p->d.precision == FSTAT_FP64
-      ? launch_pass_b_f64(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk, res, p->d_err)
-      : launch_pass_b_f32(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk, res, p->d_err);
+      ? launch_pass_b_f64(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk, res, p->d_err, p->wait_limit)
+      : launch_pass_b_f32(p->log2n1, cb, vb, Z, (int)p->n2, t.b, p->sky, out, st, pk, res, p->d_err, p->wait_limit);
 }
 
 cudaError_t launch_b_acc(fstat_plan* p, float* out, int shift, cudaStream_t st, void* Z) {
   const TwiddleTables& t = p->tt;
+  ++p->n_launches;
   return p->d.precision == FSTAT_FP64
-      ? launch_pass_b_acc_f64(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st, p->rb, p->d_err)
-      : launch_pass_b_acc_f32(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st, p->rb, p->d_err);
+      ? launch_pass_b_acc_f64(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st, p->rb, p->d_err,
+                              p->wait_limit)
+      : launch_pass_b_acc_f32(p->log2n1, p->cb, p->vb, Z, (int)p->n2, t.b, p->sky, out, shift, st, p->rb, p->d_err,
+                              p->wait_limit);
 }
 
 }  // namespace
@@ -264,7 +289,7 @@ const char* fstat_strerror(int code) {
     case FSTAT_ERR_DEGENERATE: return "degenerate antenna-pattern matrix (D <= 0)";
     case FSTAT_ERR_NONFINITE: return "non-finite value in input series";
     case FSTAT_ERR_NOT_READY: return "not every detector has data";
-    case FSTAT_ERR_UNSUPPORTED: return "size outside the supported range";
+    case FSTAT_ERR_UNSUPPORTED: return "size or phase range outside the supported limits";
     case FSTAT_ERR_TIMEOUT: return "a kernel's bounded wait for its own copies ran out";
     default: return "unknown error";
   }
@@ -277,7 +302,8 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   if (d.n_det < 1 || d.n_det > FSTAT_MAX_DET || d.dterms < 1 || d.dterms > 32 ||
       (d.precision != FSTAT_MIXED && d.precision != FSTAT_FP64) || d.interp < FSTAT_INTERP_TAPERED || d.interp > FSTAT_INTERP_PERIODIC ||
       !(d.dt > 0.0) || !std::isfinite(d.t0) || !std::isfinite(d.f_het) || d.n_samples < 1 ||
-      d.n_samples >= (int64_t(1) << 24) || !(d.ephem.c > 0.0))
+      d.n_samples >= (int64_t(1) << 24) || !(d.ephem.c > 0.0) || !std::isfinite(d.ephem.au) ||
+      (!std::isnan(d.t_ref) && !std::isfinite(d.t_ref)))
     return FSTAT_ERR_INVALID_ARG;
   int log2n = ilog2_exact(d.n_fft);
   if (log2n < 0) return FSTAT_ERR_INVALID_ARG;
@@ -287,6 +313,7 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   fstat_plan* p = new (std::nothrow) fstat_plan();
   if (!p) return FSTAT_ERR_OOM;
   p->d = d;
+  if (const char* cap = std::getenv("FSTAT_DEVICE_BYTES_CAP")) p->alloc_cap = (size_t)std::strtoull(cap, nullptr, 10);
   cudaGetDevice(&p->device);
   p->log2n = log2n;
   set_split(p, log2n / 2);
@@ -326,9 +353,9 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   const size_t zb = d.precision == FSTAT_FP64 ? 16 : 8;
   p->nblk = (int)((N + kSkyBlock - 1) / kSkyBlock);
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMalloc(&p->z, (size_t)d.n_det * N * zb);
-  if (e == cudaSuccess) e = cudaMalloc(&p->G, (size_t)(N + (int64_t(1) << kMaxLog2)) * p->pair_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&p->Z, (size_t)d.n_fft * p->pair_bytes);
+  if (e == cudaSuccess) e = palloc(p, &p->z, (size_t)d.n_det * N * zb);
+  if (e == cudaSuccess) e = palloc(p, &p->G, (size_t)(N + (int64_t(1) << kMaxLog2)) * p->pair_bytes);
+  if (e == cudaSuccess) e = palloc(p, &p->Z, (size_t)d.n_fft * p->pair_bytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
   // short transforms leave most of the GPU idle between launches: four
   // template streams up to n_fft = 2^19 (measured on GB300: 2^18 runs 1.6x
@@ -336,7 +363,7 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   p->nstream = d.n_fft <= (int64_t(1) << 19) ? 4 : 2;
   p->Zs[0] = p->Z;
   for (int k = 1; k < p->nstream && e == cudaSuccess; ++k) {
-    e = cudaMalloc(&p->Zs[k], (size_t)d.n_fft * p->pair_bytes);
+    e = palloc(p, &p->Zs[k], (size_t)d.n_fft * p->pair_bytes);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join[k], cudaEventDisableTiming);
   }
@@ -350,17 +377,17 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
     g.tab_t0 = lo;
     g.tab_inv_h = 1.0 / kTabStep;
     TimeTab* tab = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&tab, (size_t)g.tab_n * sizeof(TimeTab));
+    if (e == cudaSuccess) e = palloc(p, &tab, (size_t)g.tab_n * sizeof(TimeTab));
     p->tab = tab;
     g.tab = tab;
-    if (e == cudaSuccess) e = cudaMalloc(&p->tm_tab, (size_t)g.tab_n * kMaxDet * sizeof(double));
+    if (e == cudaSuccess) e = palloc(p, &p->tm_tab, (size_t)g.tab_n * kMaxDet * sizeof(double));
     g.tm_tab = p->tm_tab;
     if (e == cudaSuccess) e = launch_time_table(g, tab, 0);
   }
-  if (e == cudaSuccess) e = cudaMalloc(&p->partials, (size_t)3 * p->nblk * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->sky, sizeof(SkyConst));
-  if (e == cudaSuccess) e = cudaMalloc(&p->tw, (size_t)4 * (size_t(1) << kMaxLog2) * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_err, 2 * sizeof(int));
+  if (e == cudaSuccess) e = palloc(p, &p->partials, (size_t)3 * p->nblk * sizeof(double));
+  if (e == cudaSuccess) e = palloc(p, &p->sky, sizeof(SkyConst));
+  if (e == cudaSuccess) e = palloc(p, &p->tw, (size_t)4 * (size_t(1) << kMaxLog2) * 16);
+  if (e == cudaSuccess) e = palloc(p, &p->d_err, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_err, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->staged, cudaEventDisableTiming);
@@ -401,7 +428,7 @@ int prepare_series(fstat_plan* p, int det, int dtype, cudaStream_t st) {
     cudaFree(p->xh[det]);
     p->xh[det] = nullptr;
   }
-  if (!p->xh[det]) CK(cudaMalloc(&p->xh[det], (size_t)p->d.n_samples * eb));
+  if (!p->xh[det]) CK(palloc(p, &p->xh[det], (size_t)p->d.n_samples * eb));
   p->dtype[det] = dtype;
   p->have[det] = false;
   p->sky_valid = false;
@@ -517,7 +544,8 @@ int enqueue_compute(fstat_plan* p, const fstat_template* h_tmpl, const int* h_or
       int rc = run_sky(p, t0.alpha, t0.delta, st);
       if (rc) return rc;
     }
-    launch_tmpl_coef(p->sky, p->d.dt, d_tmpl, d_ord, (int)i, (int)(j - i), d_coef, st);
+    launch_tmpl_coef(p->sky, p->d.dt, p->d.n_samples, d_tmpl, d_ord, (int)i, (int)(j - i), d_coef, st);
+    ++p->n_launches;
     CK(cudaGetLastError());
     // Templates rotate over `st` and the plan's side streams, each with its
     // own intermediate, so the passes of consecutive templates overlap; the
@@ -565,6 +593,14 @@ int enqueue_compute(fstat_plan* p, const fstat_template* h_tmpl, const int* h_or
   return FSTAT_OK;
 }
 
+// Largest |tau| = |t_b - t_ref| over the data samples of any sky position:
+// the SSB grid starts within the orbital Roemer delay (au / c) of t0.
+double spin_tau_max(const fstat_plan* p) {
+  const double t_last = p->d.t0 + (double)(p->d.n_samples - 1) * p->d.dt;
+  return std::max(std::fabs(p->d.t0 - p->geo.t_ref), std::fabs(t_last - p->geo.t_ref)) +
+         p->d.ephem.au / p->d.ephem.c + p->d.dt;
+}
+
 int validate_templates(const fstat_plan* p, const fstat_template* tmpl, int64_t n) {
   if (n < 0 || (n > 0 && !tmpl) || n > INT32_MAX) return FSTAT_ERR_INVALID_ARG;
   for (int X = 0; X < p->d.n_det; ++X)
@@ -573,6 +609,10 @@ int validate_templates(const fstat_plan* p, const fstat_template* tmpl, int64_t 
     if (!std::isfinite(tmpl[i].alpha) || !std::isfinite(tmpl[i].delta) ||
         !std::isfinite(tmpl[i].f1dot) || !std::isfinite(tmpl[i].f2dot))
       return FSTAT_ERR_INVALID_ARG;
+  // spindown phase excursion within what the phase evaluation reduces exactly
+  const double tmax = spin_tau_max(p);
+  for (int64_t i = 0; i < n; ++i)
+    if (!spin_in_range(tmax, tmpl[i].f1dot, tmpl[i].f2dot)) return FSTAT_ERR_UNSUPPORTED;
   return FSTAT_OK;
 }
 
@@ -649,6 +689,7 @@ int fstat_semicoherent(fstat_plan* const* seg, int n_seg, const fstat_template* 
       if (!(std::fabs(sh) < 1e9)) return FSTAT_ERR_INVALID_ARG;
       shift[(size_t)s * n + i] = (int)sh;
       t.f1dot += t.f2dot * d_ref;
+      if (!spin_in_range(spin_tau_max(p), t.f1dot, t.f2dot)) return FSTAT_ERR_UNSUPPORTED;
       p->h_tmpl[i] = t;
       p->h_order[i] = ord[i];
     }
@@ -674,7 +715,8 @@ int fstat_semicoherent(fstat_plan* const* seg, int n_seg, const fstat_template* 
         int rc = run_sky(p, t0.alpha, t0.delta, st);
         if (rc) return rc;
       }
-      launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, (int)i, (int)(j - i), p->d_coef, st);
+      launch_tmpl_coef(p->sky, p->d.dt, p->d.n_samples, p->d_tmpl, p->d_order, (int)i, (int)(j - i), p->d_coef, st);
+      ++p->n_launches;
       CK(cudaGetLastError());
     }
     const int nq = (int)std::min<int64_t>(ns, j - i);
@@ -723,7 +765,7 @@ int peaks_request(fstat_plan* p, const fstat_peak_out* po, int64_t n_rows, int64
     if (p->keys) cudaFree(p->keys);
     p->keys = nullptr;
     p->keys_cap = 0;
-    CK(cudaMalloc(&p->keys, (size_t)*nkeys * sizeof(unsigned long long)));
+    CK(palloc(p, &p->keys, (size_t)*nkeys * sizeof(unsigned long long)));
     p->keys_cap = *nkeys;
   }
   return FSTAT_OK;
@@ -794,7 +836,7 @@ int fstat_grad(fstat_plan* p, const fstat_candidate* cand, int64_t n, float* two
       return FSTAT_ERR_INVALID_ARG;
   if (n == 0) return FSTAT_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  if (!p->gtab) CK(cudaMalloc(&p->gtab, grad_table_bytes(p->d.n_det, p->d.n_samples)));
+  if (!p->gtab) CK(palloc(p, &p->gtab, grad_table_bytes(p->d.n_det, p->d.n_samples)));
   if (!p->gtab_valid) {
     const void* xh[kMaxDet];
     for (int X = 0; X < kMaxDet; ++X) xh[X] = p->xh[X];
@@ -811,7 +853,7 @@ int fstat_grad(fstat_plan* p, const fstat_candidate* cand, int64_t n, float* two
     p->ccap = 0;
     int64_t c = std::max<int64_t>(n, 256);
     CK(cudaMallocHost(&p->h_cand, c * sizeof(fstat_candidate)));
-    CK(cudaMalloc(&p->d_cand, c * sizeof(fstat_candidate)));
+    CK(palloc(p, &p->d_cand, c * sizeof(fstat_candidate)));
     p->ccap = c;
   }
   const size_t need = grad_scratch_bytes((int)n, p->geo);
@@ -820,7 +862,7 @@ int fstat_grad(fstat_plan* p, const fstat_candidate* cand, int64_t n, float* two
     if (p->gscratch) cudaFree(p->gscratch);
     p->gscratch = nullptr;
     p->gscratch_bytes = 0;
-    CK(cudaMalloc(&p->gscratch, need));
+    CK(palloc(p, &p->gscratch, need));
     p->gscratch_bytes = need;
   }
   std::memcpy(p->h_cand, cand, (size_t)n * sizeof(fstat_candidate));
@@ -934,7 +976,7 @@ int fstat_set_streams(fstat_plan* p, int n) {
   if (!p || n < 1 || n > fstat_plan::kMaxStreams) return FSTAT_ERR_INVALID_ARG;
   CK(cudaDeviceSynchronize());
   for (int k = 1; k < n; ++k) {
-    if (!p->Zs[k]) CK(cudaMalloc(&p->Zs[k], (size_t)p->d.n_fft * p->pair_bytes));
+    if (!p->Zs[k]) CK(palloc(p, &p->Zs[k], (size_t)p->d.n_fft * p->pair_bytes));
     if (!p->side[k]) CK(cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking));
     if (!p->join[k]) CK(cudaEventCreateWithFlags(&p->join[k], cudaEventDisableTiming));
   }
@@ -963,6 +1005,18 @@ int fstat_get_residency(const fstat_plan* p, int* ra, int* rb) {
   if (!p || !ra || !rb) return FSTAT_ERR_INVALID_ARG;
   *ra = p->ra;
   *rb = p->rb;
+  return FSTAT_OK;
+}
+
+int fstat_launch_count(const fstat_plan* p, int64_t* launches) {
+  if (!p || !launches) return FSTAT_ERR_INVALID_ARG;
+  *launches = p->n_launches;
+  return FSTAT_OK;
+}
+
+int fstat_set_wait_limit(fstat_plan* p, int polls) {
+  if (!p) return FSTAT_ERR_INVALID_ARG;
+  p->wait_limit = polls < 0 ? -1 : polls;
   return FSTAT_OK;
 }
 
@@ -1092,7 +1146,7 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
     if (rc) break;
     rc = run_sky(p, 0.3, -0.5, st);
     if (rc) break;
-    launch_tmpl_coef(p->sky, p->d.dt, p->d_tmpl, p->d_order, 0, kPipe, p->d_coef, st);
+    launch_tmpl_coef(p->sky, p->d.dt, p->d.n_samples, p->d_tmpl, p->d_order, 0, kPipe, p->d_coef, st);
     // isolated timings of every compiled shape of each pass
     std::vector<std::pair<float, std::pair<int, int>>> ta, tb;
     // schedules: radix-8 first (bit 0), one buffer (bit 1), for pass B tile

@@ -13,6 +13,17 @@
 
 #include "fstat_internal.cuh"
 
+// Negative control for the parity tests (never in the regular build): with
+// FSTAT_NEGCTRL_FP32_TIMING defined, f_h t_m and the sample position
+// u = (T - t0) / dt are formed in FP32 instead of FP64, the precision loss
+// the FP64 timing exists to prevent.  A test builds this variant separately
+// and checks that its 2F fails the tolerance the regular build meets.
+#ifdef FSTAT_NEGCTRL_FP32_TIMING
+constexpr bool kNegCtrlFp32 = true;
+#else
+constexpr bool kNegCtrlFp32 = false;
+#endif
+
 namespace fstat {
 
 namespace {
@@ -169,6 +180,7 @@ __global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* _
        k += (int64_t)gridDim.x * blockDim.x) {
     double t = g.t0 + (double)k * g.dt;
     double ph = g.f_het * tm_eval(g, X, t);
+    if constexpr (kNegCtrlFp32) ph = (double)((float)g.f_het * (float)tm_eval(g, X, t));
     ph -= floor(ph);
     TIn x = xh[k];
     const double is = g.inv_sigma_ref;
@@ -212,6 +224,7 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
         T_ -= (T_ + tm - tb) / (1.0 + dtm);
       }
       double u = (T_ - g.t0) / g.dt;
+      if constexpr (kNegCtrlFp32) u = (double)((float)(T_ - g.t0) / (float)g.dt);
       long long k0 = __double2ll_rn(u);
       if (k0 < 0 || k0 > g.n - 1) continue;
       double dl = u - (double)k0;
@@ -327,37 +340,20 @@ k_sky_finalize(const double* __restrict__ partials, int nblocks, SkyConst* sky, 
 }
 
 // Per-template spindown polynomial in s = j - J (see TmplCoef).
-__global__ void k_tmpl_coef(const SkyConst* __restrict__ sky, double dt,
+__global__ void k_tmpl_coef(const SkyConst* __restrict__ sky, double dt, int64_t n,
                             const fstat_template* __restrict__ tmpl, const int* __restrict__ order,
                             int first, int count, TmplCoef* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   const fstat_template tp = tmpl[order[first + i]];
-  double jr = sky->j_ref;
-  double J = rint(jr);
-  double e = jr - J;
-  double c2 = tp.f1dot * dt * dt / 2.0;
-  double c3 = tp.f2dot * dt * dt * dt / 6.0;
-  TmplCoef c;
-  c.p[3] = c3;
-  c.p[2] = c2 - 3.0 * c3 * e;
-  c.p[1] = -2.0 * c2 * e + 3.0 * c3 * e * e;
-  c.p[0] = c2 * e * e - c3 * e * e * e;
-  for (int q = 0; q < 4; ++q) {
-    float h = (float)c.p[q];
-    c.hi[q] = h;
-    c.lo[q] = (float)(c.p[q] - (double)h);
-  }
-  c.J = (int)J;
-  c.pad_ = 0;
-  out[first + i] = c;
+  out[first + i] = spin_coef(sky->j_ref, n, dt, tp.f1dot, tp.f2dot);
 }
 
 // (after k_sky_table on the same stream: the phase uses this sky's t_m)
 template <typename TIn, typename TZ>
 void launch_phase(const Geo& g, int X, const void* xh, void* z, cudaStream_t st) {
   int blocks = (int)((g.n + 255) / 256);
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > device_sm_count() * 64) blocks = device_sm_count() * 64;
   k_detector_phase<TIn, TZ><<<blocks, 256, 0, st>>>(g, X, (const TIn*)xh, (TZ*)z + (int64_t)X * g.n);
 }
 
@@ -398,10 +394,10 @@ void launch_sky(const Geo& g, int precision, double alpha, double delta, const v
   k_sky_finalize<<<1, 1024, 0, st>>>(partials, n_blocks, sky, err);
 }
 
-void launch_tmpl_coef(const SkyConst* sky, double dt, const fstat_template* tmpl,
-                         const int* order, int first, int count, TmplCoef* out, cudaStream_t st) {
+void launch_tmpl_coef(const SkyConst* sky, double dt, int64_t n, const fstat_template* tmpl,
+                      const int* order, int first, int count, TmplCoef* out, cudaStream_t st) {
   if (count <= 0) return;
-  k_tmpl_coef<<<(count + 127) / 128, 128, 0, st>>>(sky, dt, tmpl, order, first, count, out);
+  k_tmpl_coef<<<(count + 127) / 128, 128, 0, st>>>(sky, dt, n, tmpl, order, first, count, out);
 }
 
 // Scan an input series for NaN/Inf.
@@ -416,7 +412,7 @@ __global__ void k_check_finite(const TIn* __restrict__ x, int64_t n, int* err) {
 
 void launch_check_finite(const void* x, int dtype, int64_t n, int* err, cudaStream_t st) {
   int blocks = (int)((n + 255) / 256);
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > device_sm_count() * 32) blocks = device_sm_count() * 32;
   if (dtype == FSTAT_C128) k_check_finite<double2><<<blocks, 256, 0, st>>>((const double2*)x, n, err);
   else k_check_finite<float2><<<blocks, 256, 0, st>>>((const float2*)x, n, err);
 }

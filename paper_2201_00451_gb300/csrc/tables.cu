@@ -32,6 +32,18 @@ void roots(TW* out, int log2m, cudaStream_t st) {
 
 }  // namespace
 
+int device_sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (!cached[dev]) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+    cached[dev] = sms;
+  }
+  return cached[dev];
+}
+
 TwiddleTables twiddle_layout(int precision, int log2n1, int log2n2, void* base) {
   TwiddleTables t{};
   const int log2n = log2n1 + log2n2;

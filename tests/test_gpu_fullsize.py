@@ -5,7 +5,10 @@
 * The 10-day two-detector workload at full size (1 728 000 samples,
   FFT 2^22, 10 injections), autotuned exactly as bench.py runs it: 2F at the
   injected bins and at random bins matches the oracle's direct DFT sums,
-  and each injection is recovered near its rho^2.
+  two whole rows match the oracle's FFT bin for bin, and each injection is
+  recovered near its rho^2.
+* The 120-day workload (10 368 000 samples, FFT 2^24): sampled bins of
+  several templates and one whole row against the oracle.
 """
 
 import numpy as np
@@ -116,6 +119,13 @@ def test_full_size_ten_day_two_detector_workload():
         v = got[i, inj.bin_index]
         sd = np.sqrt(2.0 * (4.0 + 2.0 * inj.rho2))
         assert abs(v - (4.0 + inj.rho2)) < 5.0 * sd + 0.02 * inj.rho2, (inj.rho2, v)
+    # two whole rows (every one of the 2^22 bins) against the oracle's FFT,
+    # so that an error confined to one tile or one split position shows
+    for i in (0, len(picks) - 1):
+        k = picks[i]
+        ref = resamp.twoF(t, prep, float(tm_all["f1dot"][k]), float(tm_all["f2dot"][k]))
+        bad = np.abs(got[i] - ref) > REL * np.abs(ref) + ABS
+        assert not bad.any(), (k, int(bad.sum()), np.flatnonzero(bad)[:8])
 
 
 def test_full_size_120_day_search_slice():
@@ -161,6 +171,11 @@ def test_full_size_120_day_search_slice():
         v = got[k, inj.bin_index]
         sd = np.sqrt(2.0 * (4.0 + 2.0 * inj.rho2))
         assert abs(v - (4.0 + inj.rho2)) < 5.0 * sd + 0.02 * inj.rho2, (inj.rho2, v)
+    # one whole row (all 2^24 bins) against the oracle's FFT
+    key = (float(rows["alpha"][0]), float(rows["delta"][0]))
+    ref = resamp.twoF(t, preps[key], float(rows["f1dot"][0]), float(rows["f2dot"][0]))
+    bad = np.abs(got[0] - ref) > REL * np.abs(ref) + ABS
+    assert not bad.any(), (int(bad.sum()), np.flatnonzero(bad)[:8])
 
 
 def test_full_size_peaks_and_semicoherent_agree_with_dense_passes():

@@ -253,3 +253,30 @@ def test_register_caps_and_tma_loads_give_identical_2F():
             with pytest.raises(pkg.FstatError):
                 plan.set_cta(*bad)
     assert_parity(base, resamp.fstat(t, x, tm))
+
+
+@pytest.mark.parametrize("t_ref_days", [-40.0, -450.0, 500.0])
+def test_reference_time_far_outside_the_data(t_ref_days):
+    # A spindown reference time far from the data (up to ~2.2e7 samples of
+    # 2 s away, beyond the 2^24 sample offsets FP32 holds exactly): the phase
+    # polynomial is expanded about the data sample nearest t_ref, so the
+    # sample offsets stay below the data length and 2F still matches the
+    # oracle.
+    t = small(seed=31, t_ref=t_ref_days * 86400.0, f1dots=(-3e-13, 0.0, 2e-13), f2dots=(0.0, 2e-21))
+    x = synth.make_data(t)
+    tm = t.templates()
+    assert_parity(run_gpu(t, x, tm), resamp.fstat(t, x, tm))
+
+
+def test_spindown_phase_excursion_beyond_range_is_rejected():
+    # |f1dot| tau^2 over the data above 2^20 cycles cannot be reduced exactly
+    # in the FP32 path's phase evaluation: the call is refused, not computed.
+    t = small(seed=32, t_ref=-400.0 * 86400.0, f1dots=(1e-9,), f2dots=(0.0,))
+    x = synth.make_data(t)
+    with pkg.FstatPlan.from_target(t) as plan:
+        for X in range(2):
+            plan.set_data(X, x[X], t.sigmas[X])
+        with pytest.raises(pkg.FstatError) as e:
+            plan.compute(t.templates())
+        assert e.value.code == -7
+        plan.sync()
