@@ -1,18 +1,22 @@
 """Throughput benchmark of the resampling F-statistic on one GB300 (or N replicas).
 
-Workload: the narrowband single-target search (H1 + L1, 10 days at dt = 0.5 s,
-1 728 000 complex64 samples per detector, FFT 2^22, one sky position,
-8192 f1dot x 4 f2dot = 32 768 templates), seeded Gaussian noise.  One step is
-the whole hot path over that job: per-sky work (Sec. 3 steps iii-v) plus
-steps vi-vii for all 32 768 templates, 2F written for every bin.
+Headline workload: the large narrowband search (H1 + L1, 120 days at
+dt = 1 s, 10 368 000 complex64 samples per detector, FFT 2^24, a 1' x 1'
+patch of 64 sky positions x 2048 f1dot x 8 f2dot).  One step is one sky
+position of that bank: the per-sky work (Sec. 3 steps iii-v) plus steps
+vi-vii for its 16 384 spindown templates, 2F written for every bin.  Every
+sky position costs the same, so templates/s of a step is the job's rate;
+replicas (--gpus N) take different sky positions.
 
 Printed JSON line: templates/s (value), 2F-bins/s, the dominant kernel's
-HBM and FP32 rooflines, the FP64-GPU comparison path, the oracle on the
-host cores, end-to-end through host buffers (e2e: 2F reduced on the device
-to band maxima and 2F > 70; e2e_dense: every bin read back), further
-workloads (one CUDA graph, uneven targets, 120-day search, refinement,
-semi-coherent segments, interpolator costs), and clocks sampled during the
-timed region.
+roofline from a serialised pass (one template stream, so no other kernel
+overlaps the events), the whole path's HBM and FP32 fractions against
+measured peaks, the FP64-GPU comparison path, cuFFT for the same
+transforms, the oracle on the host cores, end-to-end through host buffers
+(e2e: pinned x_h up, 2F reduced on the device to band maxima and 2F > 70,
+results down), further workloads (the 10-day narrowband search, one CUDA
+graph, uneven targets, refinement, semi-coherent segments, interpolator
+costs), and clocks sampled during the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -20,6 +24,7 @@ timed region.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -39,8 +44,20 @@ from workloads import config2, config3, config5, make_noise, template_grid  # no
 
 METRIC = "templates/s and 2F-bins/s on 1 GB300 at |d2F|<=1e-3·2F+0.02 vs plain FP64-GPU path"
 UNIT = "templates/s"
-WORKLOAD = ("narrowband single target: H1+L1, 10 d, dt=0.5 s, 1,728,000 c64 samples/det, "
-            "FFT 2^22, 1 sky x 8192 f1dot x 4 f2dot = 32,768 templates, Dterms 8")
+WORKLOAD = ("large narrowband search, one sky position per step: H1+L1, 120 d, dt=1 s, "
+            "10,368,000 c64 samples/det, FFT 2^24, per-sky work + 2048 f1dot x 8 f2dot = 16,384 "
+            "templates (1 of the 64 sky positions of the 1'x1' patch bank), Dterms 8")
+NARROW = ("narrowband single target: H1+L1, 10 d, dt=0.5 s, 1,728,000 c64 samples/det, "
+          "FFT 2^22, 1 sky x 8192 f1dot x 4 f2dot = 32,768 templates, Dterms 8")
+
+
+def headline_config(world: int) -> dict:
+    """The ``config`` object both arms print (the driver compares them)."""
+    return {"workload": WORKLOAD, "templates_per_step": 16384, "sky_positions_in_job": 64,
+            "n_fft": 1 << 24, "n_samples": 10_368_000,
+            "l2": "flushed between steps (256 MB write, untimed); inputs (2 x 83 MB x_h, 166 MB "
+                  "resampled series) exceed the 126 MB L2",
+            "parallelism": f"replicas x{world}"}
 
 
 def parse():
@@ -49,21 +66,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--templates", type=int, default=0, help="templates per step (0 = full job)")
-    ap.add_argument("--chunk", type=int, default=256, help="templates per fstat_compute call")
-    ap.add_argument("--fp64-templates", type=int, default=8)
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--no-refine", action="store_true")
-    ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--no-uneven", action="store_true")
-    ap.add_argument("--no-large", action="store_true")
-    ap.add_argument("--no-interp", action="store_true")
-    ap.add_argument("--no-semicoh", action="store_true")
-    ap.add_argument("--no-skyheavy", action="store_true")
-    ap.add_argument("--no-sft", action="store_true")
-    ap.add_argument("--streams", type=int, default=2, help="template streams per plan (1..8)")
+    ap.add_argument("--chunk", type=int, default=64, help="templates per fstat_compute call")
+    ap.add_argument("--extra-steps", type=int, default=3, help="timed steps of the further workloads")
+    ap.add_argument("--fp64-templates", type=int, default=4)
+    for leg in ("e2e", "cpu", "fp64", "refine", "graph", "uneven", "narrow", "interp", "semicoh", "skyheavy",
+                "sft", "cufft", "probe"):
+        ap.add_argument(f"--no-{leg}", action="store_true")
+    ap.add_argument("--streams", type=int, default=0, help="template streams per plan (0 = the plan's default)")
     ap.add_argument("--shape", default="", help="n1,ca,va,cb,vb: fixed FFT split and CTA shapes (skip autotune)")
     return ap.parse_args()
 
@@ -189,106 +198,162 @@ def make_inputs(t, rank):
 
 
 # ------------------------------------------------------------- CPU oracle
-def cpu_oracle_timing(t, xs, n_tmpl_total, n_sample_tmpl=2):
-    """The FP64 oracle as it stands on a bounded sample: one per-sky step
-    (iii-v) and ``n_sample_tmpl`` templates of steps vi-vii, extrapolated to
-    the full job."""
+def oracle_sample(t, xs, sky, n_tmpl, warmup=0, part=8):
+    """The FP64 oracle as it stands, on a bounded sample of one sky
+    position's work: the per-sky step (iii-v) on the first 1/part of the
+    samples (its cost is linear in the sample count, so it is scaled by
+    part), then steps vi-vii of ``warmup`` untimed and ``n_tmpl`` timed
+    templates at the full size (the full-length per-sky series is the
+    sample's, repeated; the FFT's cost does not depend on the values).
+    Returns (per-sky seconds, [per-template seconds])."""
     from oracle import resamp
 
-    a, d = t.skies[0]
-    t0 = time.perf_counter()
-    prep = resamp.sky_prep(t, xs, a, d)
-    t_sky = time.perf_counter() - t0
-    tm = t.templates()
-    times = []
-    for k in range(n_sample_tmpl):
-        s = time.perf_counter()
-        resamp.twoF(t, prep, float(tm["f1dot"][k]), float(tm["f2dot"][k]))
-        times.append(time.perf_counter() - s)
-    t_tmpl = sum(times) / len(times)
-    value = n_tmpl_total / (t_sky + n_tmpl_total * t_tmpl)
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 per-sky step (2 det x {t.n_samples} samples) in {t_sky:.2f} s + "
-                      f"{n_sample_tmpl} templates of 2 x 2^{int(math.log2(t.n_fft))} FFTs at "
-                      f"{t_tmpl:.2f} s each, extrapolated to {n_tmpl_total} templates"}, t_sky, t_tmpl
-
-
-def _oracle_worker(job):
-    """One host process of the all-cores oracle timing: the per-sky step,
-    then templates of steps vi-vii; returns (per-sky s, [per-template s])."""
-    t, xs, ks = job
-    from oracle import resamp
-
-    a, d = t.skies[0]
+    n = t.n_samples // part
+    ts = dataclasses.replace(t, n_samples=n, injections=(), name=t.name + ".sample")
     s = time.perf_counter()
-    prep = resamp.sky_prep(t, xs, a, d)
-    t_sky = time.perf_counter() - s
-    tm = t.templates()
+    prep = resamp.sky_prep(ts, [np.asarray(x[:n], dtype=np.complex128) for x in xs], *sky)
+    t_sky = (time.perf_counter() - s) * t.n_samples / n
+    full = dict(prep)
+    full["Ga"] = np.resize(prep["Ga"], t.n_samples)
+    full["Gb"] = np.resize(prep["Gb"], t.n_samples)
+    f1, f2 = t.f1dots, t.f2dots
+    for k in range(warmup):
+        resamp.twoF(t, full, float(f1[k % len(f1)]), float(f2[0]))
     times = []
-    for k in ks:
+    for k in range(n_tmpl):
         s = time.perf_counter()
-        resamp.twoF(t, prep, float(tm["f1dot"][k]), float(tm["f2dot"][k]))
+        resamp.twoF(t, full, float(f1[(k + warmup) % len(f1)]), float(f2[k % len(f2)]))
         times.append(time.perf_counter() - s)
     return t_sky, times
 
 
-def cpu_oracle_all_cores(t, xs, n_tmpl_total, n_per_worker=2):
-    """The same oracle in one process per host core (spawned), all working
-    at once on different templates; the job extrapolates as one per-sky step
-    plus n_tmpl_total templates spread over the cores."""
+def _oracle_worker(job):
+    """One host process of the all-cores oracle timing: steps vi-vii of
+    ``k`` templates of the full size on seeded per-sky series."""
+    t, seed, k = job
+    from oracle import resamp
+
+    rng = np.random.default_rng(seed)
+    prep = {"Ga": rng.standard_normal(t.n_samples) + 1j * rng.standard_normal(t.n_samples),
+            "Gb": rng.standard_normal(t.n_samples) + 1j * rng.standard_normal(t.n_samples),
+            "A": 1.0, "B": 1.0, "C": 0.1, "D": 0.99, "t_b0": t.t0}
+    times = []
+    for i in range(k):
+        s = time.perf_counter()
+        resamp.twoF(t, prep, float(t.f1dots[i]), float(t.f2dots[0]))
+        times.append(time.perf_counter() - s)
+    return times
+
+
+def cpu_oracle_all_cores(t, t_sky_1core, n_tmpl, n_per_worker=1):
+    """Steps vi-vii of the oracle in one spawned process per host core, all
+    at once; the per-sky step enters as its 1-core time spread over the
+    cores (it splits into independent sample ranges)."""
     import concurrent.futures as cf
     import multiprocessing as mp
 
     workers = os.cpu_count() or 1
-    n_t = t.n_templates
-    jobs = [(t, xs, [(w * n_per_worker + i) % n_t for i in range(n_per_worker)]) for w in range(workers)]
+    jobs = [(t, 1000 + w, n_per_worker) for w in range(workers)]
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         res = list(ex.map(_oracle_worker, jobs))
-    t_sky = statistics.median(r[0] for r in res)
-    t_tmpl = statistics.median(x for r in res for x in r[1])
-    value = n_tmpl_total / (t_sky + n_tmpl_total * t_tmpl / workers)
+    t_tmpl = statistics.median(x for r in res for x in r)
+    value = n_tmpl / ((t_sky_1core + n_tmpl * t_tmpl) / workers)
     return {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
-            "sample": f"{workers} spawned processes at once, each 1 per-sky step (median {t_sky:.2f} s) + "
-                      f"{n_per_worker} templates (median {t_tmpl:.2f} s each), extrapolated to "
-                      f"{n_tmpl_total} templates over {workers} cores"}
+            "sample": f"{workers} spawned processes at once, each {n_per_worker} template(s) of steps vi-vii "
+                      f"at FFT 2^{int(math.log2(t.n_fft))} (median {t_tmpl:.2f} s); per-sky step "
+                      f"{t_sky_1core:.1f} s (1 core, from a 1/8 sample) spread over the cores; "
+                      f"{n_tmpl} templates per sky position"}
 
 
 # ------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on
+    the headline workload's sky position.  Each timed step is one template
+    of steps vi-vii at full size (2 x 2^24-point FFTs); the per-sky step is
+    timed once on a 1/8 sample and scaled.  value = templates/s of a whole
+    sky position (per-sky step + 16 384 templates)."""
     if rank != 0:
         return
-    t = config2()
+    t = config5()
     xs = make_inputs(t, 0)
-    from oracle import resamp
-
-    a, d = t.skies[0]
-    s = time.perf_counter()
-    prep = resamp.sky_prep(t, xs, a, d)
-    t_sky = time.perf_counter() - s
-    tm = t.templates()
-    for k in range(args.warmup):
-        resamp.twoF(t, prep, float(tm["f1dot"][k]), float(tm["f2dot"][k]))
-    times = []
-    for k in range(args.steps):
-        s = time.perf_counter()
-        resamp.twoF(t, prep, float(tm["f1dot"][k]), float(tm["f2dot"][k]))
-        times.append(time.perf_counter() - s)
-    n = t.n_templates
+    t_sky, times = oracle_sample(t, xs, t.skies[0], args.steps, warmup=args.warmup)
+    n = 16384
     t_tmpl = sum(times) / len(times)
     value = n / (t_sky + n * t_tmpl)
-    sample = (f"per-sky step once ({t_sky:.2f} s) + one template per step ({t_tmpl:.2f} s), "
-              f"extrapolated to {n} templates")
+    sample = (f"per-sky step {t_sky:.1f} s (timed on 1/8 of the samples, scaled by 8) + {args.steps} timed "
+              f"template(s) of steps vi-vii at {t_tmpl:.2f} s each after {args.warmup} untimed; value = "
+              f"{n} / (per-sky + {n} x per-template)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": (t_sky + n * t_tmpl) * 1e3,
+            "warmup": args.warmup, "ms_per_step": t_tmpl * 1e3,
+            "step": "one template of steps vi-vii (the oracle's unit of work); ms_per_step is its measured time",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "config": headline_config(world),
+            "setup": {"precision": "FP64 throughout (the oracle, NumPy complex128)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------ our arm
+PASS_BYTES = {0: "pass_a", 1: "pass_b", 3: "fused"}
+
+
+def serial_roofline(plan, t, tm, out, stream, n=32):
+    """Per-kernel CUDA-event times from a serialised pass (one template
+    stream: no other kernel of the plan overlaps a launch's events), and
+    each kernel's algorithmic bytes per launch: pass A reads G_a, G_b
+    (16 B per sample), pass B writes 2F (4 B per bin), a fused launch does
+    both for every template it covers.  Returns {kind: (launches, total ms,
+    bytes per launch)}."""
+    plan.set_streams(1)
+    plan.compute_ptr(tm[:2], out.data_ptr(), stream)
+    plan.sync()
+    plan.set_profiling(True)
+    plan.compute_ptr(tm[:n], out.data_ptr(), stream)
+    plan.sync()
+    res = {}
+    for k in (0, 1, 3):
+        nl, tot = plan.kernel_stats(k)
+        if nl:
+            per_launch = {0: 16.0 * t.n_samples, 1: 4.0 * t.n_fft,
+                          3: (16.0 * t.n_samples + 4.0 * t.n_fft) * n / max(nl, 1)}[k]
+            res[k] = (nl, tot, per_launch)
+    plan.set_profiling(False)
+    return res
+
+
+def roofline_line(serial, t, value_per_gpu, hbm_peak, peak_kind, f32_peak, f32_kind, plan, ms_per_template):
+    dom = max(serial, key=lambda k: serial[k][1])
+    nl, tot, bytes_alg = serial[dom]
+    avg_s = tot / 1e3 / nl
+    achieved = bytes_alg / avg_s / 1e9
+    n1, n2 = plan.split
+    ca, va, cb, vb = plan.cta
+    shape = {0: (n2, ca, va), 1: (n1, cb, vb), 3: (n1 * n2, ca, cb)}[dom]
+    bpt = 16.0 * t.n_samples + 4.0 * t.n_fft
+    flops_t = 2 * 5 * t.n_fft * math.log2(t.n_fft)
+    serial_ms = sum(v[1] / v[0] for k, v in serial.items() if k in (0, 1))
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": ncu_traffic(PASS_BYTES[dom], *shape),
+            "kernel": PASS_BYTES[dom], "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy)",
+            "timing": f"serialised pass: one template stream, {nl} launches, CUDA events per launch",
+            "kernel_ms_per_launch": avg_s * 1e3, "bytes_per_launch": bytes_alg,
+            "kernels": {PASS_BYTES[k]: {"launches": v[0], "ms_per_launch": v[1] / v[0],
+                                        "GBps": v[2] / (v[1] / v[0] / 1e3) / 1e9,
+                                        "frac": v[2] / (v[1] / v[0] / 1e3) / 1e9 / hbm_peak}
+                        for k, v in serial.items()},
+            "serialised_ms_per_template": serial_ms if serial_ms else None,
+            "pipelined_ms_per_template": ms_per_template,
+            "path": {"bytes_per_template": bpt, "achieved_GBps": bpt * value_per_gpu / 1e9,
+                     "frac": bpt * value_per_gpu / 1e9 / hbm_peak},
+            "alu": {"unit": "TFLOP/s", "peak": f32_peak, "peak_source": f32_kind,
+                    "flops_per_template": flops_t,
+                    "path_achieved": flops_t * value_per_gpu / 1e12,
+                    "path_frac": flops_t * value_per_gpu / 1e12 / f32_peak},
+            "split": [n1, n2], "cta": list(plan.cta)}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -304,18 +369,28 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
 
-    t = config2()
+    # measured FMA peaks of this GPU (denominators of the ALU fractions)
+    probe = None
+    if not args.no_probe:
+        f32, ms32 = pkg.probe_fma(pkg.MIXED, 1 << 16, stream)
+        f64, ms64 = pkg.probe_fma(pkg.FP64, 1 << 12, stream)
+        probe = {"fp32_fma_tflops": f32, "fp64_fma_tflops": f64, "fp32_ms": ms32, "fp64_ms": ms64,
+                 "how": "fstat_probe_fma: 8 independent FMA chains per thread, 2048 threads per SM on every "
+                        "SM, CUDA events, after one warm-up launch"}
+
+    t = config5()
     xs = make_inputs(t, rank)
-    tm_all = pkg.as_templates(t.templates())
-    n_tmpl = args.templates or len(tm_all)
-    tm = tm_all[:n_tmpl] if n_tmpl <= len(tm_all) else np.resize(tm_all, n_tmpl)
+    sky = t.skies[rank % len(t.skies)]
+    tm = pkg.as_templates(template_grid((sky,), t.f1dots, t.f2dots))
+    n_tmpl = len(tm)
     chunk = min(args.chunk, n_tmpl)
     n_fft = t.n_fft
 
     plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
     for X in range(len(t.detectors)):
         plan.set_data(X, xs[X], t.sigmas[X])
-    plan.set_streams(args.streams)
+    if args.streams:
+        plan.set_streams(args.streams)
     set_shape(plan, args, stream)
     out = torch.empty((chunk, n_fft), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > L2
@@ -338,8 +413,8 @@ def run_ours(args, rank, world, local_rank):
 
     clocks = ClockSampler(local_rank)
     clocks.start()
-    plan.set_profiling(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = plan.launches
     for k in range(args.steps):
         flush.zero_()                      # untimed: evict L2 between steps
         barrier()
@@ -347,54 +422,24 @@ def run_ours(args, rank, world, local_rank):
         step()
         ev[k][1].record(stream)
         barrier()
+    launches = plan.launches - l0
     plan.sync()
     clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    stats = {k: plan.kernel_stats(k) for k in (0, 1, 2)}
-    plan.set_profiling(False)
     ms = reduce_max(ms, world, dev)
     total_tmpl = n_tmpl * args.steps * world
     value = total_tmpl / (ms / 1e3)
-    # per step: the per-sky kernels (setup, delay table, step iii per detector,
-    # resampling, finalize), one coefficient kernel per chunk, two passes per template
-    launches = args.steps * (len(chunks) + 2 * n_tmpl + 4 + len(t.detectors))
-
-    # dominant kernel roofline (algorithmic bytes: 16 B per sample read for
-    # pass A, 4 B per bin written for pass B)
-    peak, peak_kind = peaks()
-    n1, n2 = plan.split
-    kinfo = {0: ("pass_a", 16.0 * t.n_samples), 1: ("pass_b", 4.0 * n_fft)}
-    dom = max((0, 1), key=lambda k: stats[k][1])
-    nl, tot = stats[dom]
-    avg_s = tot / 1e3 / max(nl, 1)
-    name, bytes_alg = kinfo[dom]
-    achieved = bytes_alg / avg_s / 1e9
-    ca, va, cb, vb = plan.cta
-    shape = (n2, ca, va) if dom == 0 else (n1, cb, vb)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": ncu_traffic(name, *shape), "kernel": name,
-            "kernel_shape": {"L": shape[0], "c": shape[1], "v": shape[2]},
-            "peak_source": peak_kind,
-            "kernels_ms_per_launch": {kinfo[k][0]: stats[k][1] / max(stats[k][0], 1) for k in (0, 1)},
-            "per_sky_ms": stats[2][1] / max(stats[2][0], 1),
-            "path": {"bytes_per_template": 16.0 * t.n_samples + 4.0 * n_fft,
-                     "achieved_GBps": (16.0 * t.n_samples + 4.0 * n_fft) * value / world / 1e9,
-                     "frac": (16.0 * t.n_samples + 4.0 * n_fft) * value / world / 1e9 / peak},
-            "split": [n1, n2], "cta": list(plan.cta)}
-    # the FFT's arithmetic against the FP32 CUDA-core peak (5 N log2 N flops
-    # per complex transform, two transforms per template; the FP32 peak is
-    # SMs x 128 lanes x 2 flops x SM clock)
-    props = torch.cuda.get_device_properties(dev)
-    f32_peak = props.multi_processor_count * 128 * 2 * FP32_CLOCK_MHZ * 1e6 / 1e12
-    flops_t = 2 * 5 * n_fft * math.log2(n_fft)
-    flops_k = {0: 2 * 5 * n_fft * math.log2(n2), 1: 2 * 5 * n_fft * math.log2(n1)}
-    roof["alu"] = {"unit": "TFLOP/s", "peak": f32_peak, "peak_source": "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                   "flops_per_template": flops_t,
-                   "path_achieved": flops_t * value / world / 1e12,
-                   "path_frac": flops_t * value / world / 1e12 / f32_peak,
-                   "kernel_achieved": flops_k[dom] / avg_s / 1e12,
-                   "kernel_frac": flops_k[dom] / avg_s / 1e12 / f32_peak}
+    per_gpu = value / world
+    hbm_peak, peak_kind = peaks()
+    serial = serial_roofline(plan, t, tm, out, stream)
+    f32_peak, f32_kind = ((probe["fp32_fma_tflops"], "measured: fstat_probe_fma FP32") if probe else
+                          (torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2 * 2.07e9 / 1e12,
+                           "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz"))
+    roof = roofline_line(serial, t, per_gpu, hbm_peak, peak_kind, f32_peak, f32_kind, plan,
+                         ms / args.steps / n_tmpl)
+    split, cta = plan.split, plan.cta
     plan.close()
+    del out
 
     line = None
     if rank == 0:
@@ -403,70 +448,137 @@ def run_ours(args, rank, world, local_rank):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "bins_per_s": value * n_fft,
                 "tau_F_eff_s": 1.0 / (value * n_fft * len(t.detectors)),
-                "config": {"workload": WORKLOAD, "templates_per_step": n_tmpl, "chunk": chunk,
-                           "streams": args.streams,
-                           "precision": "mixed: FP64 timing and phases, FP32 resample/FFT/2F",
-                           "l2": "flushed between steps (256 MB write, untimed)",
-                           "parallelism": f"replicas x{world}"},
+                "job_hours_64_sky": 64 * n_tmpl / per_gpu / 3600.0,
+                "config": headline_config(world),
+                "setup": {"precision": "mixed: FP64 timing and phases, FP32 resample/FFT/2F",
+                          "chunk": chunk, "streams": args.streams or "plan default"},
                 "roofline": roof, "gpu_launches": launches, "clocks": clocks.summary()}
+        if probe:
+            line["peaks_probe"] = probe
+        line["setup"]["shape"] = {"split": list(split), "cta": list(cta)}
 
-    # the same step replayed as one CUDA graph (per-sky work + all templates)
-    if rank == 0 and not args.no_graph:
-        line["graph"] = graph_bench(t, xs, tm, chunk, dev, stream, args, flush)
+    def leg(name, fn, flag=None):
+        # a further workload; its failure is reported, not fatal to the line
+        if rank != 0 or getattr(args, "no_" + (flag or name.split("_")[0]), False):
+            return
+        try:
+            line[name] = fn()
+        except Exception as e:  # noqa: BLE001
+            line[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.synchronize(dev)
 
-    # batched uneven targets (different spans, bands, FFT lengths) in one graph
-    if rank == 0 and not args.no_uneven:
-        line["uneven_targets"] = uneven_bench(dev, stream)
-
-    # large search (120 d, FFT 2^24, 64 skies x 16384 spindowns): a bounded slice
-    if rank == 0 and not args.no_large:
-        line["large_search"] = large_bench(dev, stream)
-
-    # sky-dominated bank (many sky positions, few spindowns)
-    if rank == 0 and not args.no_skyheavy:
-        line["sky_heavy"] = sky_heavy_bench(t, xs, dev, stream, args)
-
-    # step (ii): x_h from SFTs on the device, once per data set
-    if rank == 0 and not args.no_sft:
-        line["sft_to_xh"] = sft_bench(t, dev)
-
-    # semi-coherent search: ten 10-day segments summed on the device
-    if rank == 0 and not args.no_semicoh:
-        line["semicoherent"] = semicoh_bench(dev, stream, args)
-
-    # per-sky cost of the step-(v) interpolator variants and half-widths
-    if rank == 0 and not args.no_interp:
-        line["interp_cost"] = interp_cost(t, xs, tm_all, dev, stream)
-
-    # FP64-GPU comparison path (same kernels in FP64), timed on a subset
-    if rank == 0 and not args.no_fp64:
-        line["fp64_gpu"] = fp64_gpu(t, xs, tm_all, args.fp64_templates, dev, stream, value)
-
-    # differentiable refinement: 4096 candidates x 20 gradient-ascent steps
-    if rank == 0 and not args.no_refine:
-        line["refine"] = refine_bench(t, xs, dev)
-
-    # end-to-end through the public API: pinned host x_h -> device, every
-    # bin's 2F computed and reduced on the device (band maxima and 2F > 70,
-    # the retention of Sec. 5.4), results back to pinned host memory; and the
-    # same job reading back every bin's 2F (550 GB per step)
-    if rank == 0 and not args.no_e2e:
-        line["e2e"] = e2e_peaks(t, xs, tm, chunk, dev, stream, args)
-        line["e2e_dense"] = e2e(t, xs, tm, chunk, dev, stream, args)
+    ksteps = max(1, min(args.steps, args.extra_steps))
+    # FP64-GPU comparison path (same kernels in FP64) on the headline workload
+    leg("fp64_gpu", lambda: fp64_gpu(t, xs, tm, args.fp64_templates, dev, stream, per_gpu))
+    # cuFFT (through torch.fft) for the same transforms, comparison only
+    leg("cufft", lambda: cufft_bench(dev, stream, per_gpu))
+    # end to end through the public API: pinned host x_h -> device, every
+    # bin's 2F reduced on the device (band maxima and 2F > 70, the retention
+    # of Sec. 5.4), results back to pinned host memory
+    leg("e2e", lambda: e2e_peaks(t, xs, tm, chunk, dev, stream, args, ksteps))
+    xs = None
+    # the 10-day narrowband search (FFT 2^22) as before, and further workloads
+    t2 = config2()
+    xs2 = make_inputs(t2, rank)
+    tm2 = pkg.as_templates(t2.templates())
+    leg("narrow", lambda: narrow_bench(t2, xs2, tm2, dev, stream, args, ksteps, flush, hbm_peak, peak_kind,
+                                       f32_peak, f32_kind))
+    leg("graph", lambda: graph_bench(t2, xs2, tm2, 256, dev, stream, ksteps, flush))
+    leg("uneven_targets", lambda: uneven_bench(dev, stream, ksteps))
+    leg("sky_heavy", lambda: sky_heavy_bench(t2, xs2, dev, stream, ksteps), "skyheavy")
+    leg("sft_to_xh", lambda: sft_bench(t2, dev))
+    leg("semicoherent", lambda: semicoh_bench(dev, stream, ksteps), "semicoh")
+    leg("interp_cost", lambda: interp_cost(t2, xs2, tm2, dev, stream))
+    leg("refine", lambda: refine_bench(t2, xs2, dev))
+    leg("e2e_dense_narrowband", lambda: e2e(t2, xs2, tm2, 256, dev, stream, 1), "e2e")
 
     if rank == 0 and not args.no_cpu:
-        x64 = [x.astype(np.complex128) for x in xs]
-        cb, _, _ = cpu_oracle_timing(t, x64, len(tm_all))
-        line["cpu_baseline"] = cb
-        line["cpu_baseline_all_cores"] = cpu_oracle_all_cores(t, x64, len(tm_all))
+        xs = make_inputs(t, 0)
+        t_sky, times = oracle_sample(t, xs, sky, 2)
+        t_tmpl = sum(times) / len(times)
+        cpu_v = n_tmpl / (t_sky + n_tmpl * t_tmpl)
+        line["cpu_baseline"] = {
+            "value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"per-sky step {t_sky:.1f} s (timed on 1/8 of the 2 x 10,368,000 samples, scaled by 8) + "
+                      f"2 templates of steps vi-vii (2 x 2^24-point FFTs) at {t_tmpl:.2f} s each; value = "
+                      f"{n_tmpl} / (per-sky + {n_tmpl} x per-template)"}
+        line["cpu_baseline_all_cores"] = cpu_oracle_all_cores(t, t_sky, n_tmpl)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def cufft_bench(dev, stream, mixed_value, reps=10):
+    """cuFFT through torch.fft on the same transforms as one template's
+    steps vi-vii (two complex64 C2C transforms of 2^24 and of 2^22 points),
+    timed with CUDA events after warm-up; comparison only (the library's
+    FFT is its own)."""
+    import torch
+
+    res = {}
+    for log2n in (22, 24):
+        x = torch.randn((2, 1 << log2n), dtype=torch.complex64, device=dev)
+        for _ in range(3):
+            torch.fft.fft(x)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            torch.fft.fft(x)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        res[f"2x2^{log2n}_ms"] = a.elapsed_time(b) / reps
+        del x
+    res["note"] = ("two C2C transforms only (no spindown phase, no 2F, no zero-padding skip); the library's "
+                   "whole template at 2^24 takes 1/value")
+    res["ours_ms_per_template_2e24"] = 1e3 / mixed_value
+    return res
+
+
+def narrow_bench(t, xs, tm, dev, stream, args, steps, flush, hbm_peak, peak_kind, f32_peak, f32_kind,
+                 chunk=256):
+    """The 10-day narrowband search (FFT 2^22, 32 768 templates of one sky
+    position per step, per-sky work included, L2 flushed between steps),
+    and its serialised per-kernel roofline."""
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+
+    plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
+    for X in range(len(t.detectors)):
+        plan.set_data(X, xs[X], t.sigmas[X])
+    plan.autotune(stream)
+    out = torch.empty((chunk, t.n_fft), dtype=torch.float32, device=dev)
+    chunks = [tm[i:i + chunk] for i in range(0, len(tm), chunk)]
+
+    def step():
+        plan.invalidate_sky()
+        for c in chunks:
+            plan.compute_ptr(c, out.data_ptr(), stream)
+
+    step()
+    torch.cuda.synchronize(dev)
+    ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms += a.elapsed_time(b)
+    value = len(tm) * steps / (ms / 1e3)
+    serial = serial_roofline(plan, t, tm, out, stream)
+    roof = roofline_line(serial, t, value, hbm_peak, peak_kind, f32_peak, f32_kind, plan, ms / steps / len(tm))
+    plan.close()
+    return {"value": value, "unit": UNIT, "bins_per_s": value * t.n_fft, "ms_per_step": ms / steps,
+            "workload": NARROW, "roofline": roof}
 
 
 SEMI_SEGMENTS = 10
 
 
-def semicoh_bench(dev, stream, args, n_f1=256, n_f2=2):
+def semicoh_bench(dev, stream, steps, n_f1=256, n_f2=2):
     """Semi-coherent search (Sec. 6): ten consecutive 10-day segments of
     H1 + L1 data (each 1 728 000 c64 samples, FFT 2^22, its own reference
     time), 1 sky x 256 f1dot x 2 f2dot templates at the global reference
@@ -498,16 +610,15 @@ def semicoh_bench(dev, stream, args, n_f1=256, n_f2=2):
             p.invalidate_sky()
         pkg.semicoherent(plans, tm, t_ref, out=out, stream=stream)
 
-    for _ in range(max(args.warmup, 1)):
-        step()
+    step()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    sec = e0.elapsed_time(e1) * 1e-3 / args.steps
+    sec = e0.elapsed_time(e1) * 1e-3 / steps
     for p in plans:
         p.close()
     return {"value": len(tm) / sec, "unit": "semi-coherent templates/s",
@@ -549,6 +660,9 @@ def interp_cost(t, xs, tm_all, dev, stream, reps=5):
 
 
 def fp64_gpu(t, xs, tm_all, n, dev, stream, mixed_value):
+    """The plain FP64-GPU path (the same kernels in FP64, complex128 FFT) on
+    the headline workload: per-sky work plus n templates, extrapolated to
+    one sky position's bank."""
     import torch
 
     import paper_2201_00451_gb300 as pkg
@@ -572,13 +686,14 @@ def fp64_gpu(t, xs, tm_all, n, dev, stream, mixed_value):
     n_sky, ms_sky = plan.kernel_stats(2)
     plan.close()
     per_t = (ms - ms_sky) / n
-    total = t.n_templates
+    total = len(tm_all)
     v = total / ((ms_sky + total * per_t) / 1e3)
-    return {"value": v, "unit": UNIT, "sample": f"per-sky step + {n} templates, extrapolated to {total}",
+    return {"value": v, "unit": UNIT, "sample": f"per-sky step ({ms_sky:.1f} ms) + {n} templates at "
+                                               f"{per_t:.2f} ms, extrapolated to {total} templates",
             "mixed_over_fp64": mixed_value / v}
 
 
-def graph_bench(t, xs, tm, chunk, dev, stream, args, flush):
+def graph_bench(t, xs, tm, chunk, dev, stream, steps, flush):
     """The bench step captured once as a CUDA graph (fstat_batch with an
     output ring of `chunk` rows) and replayed: same work, no per-kernel host
     launches and no timing events."""
@@ -594,11 +709,10 @@ def graph_bench(t, xs, tm, chunk, dev, stream, args, flush):
     batch = pkg.FstatBatch()
     batch.add(plan, tm, out, out_rows=chunk)
     batch.instantiate(stream)
-    for _ in range(max(1, args.warmup - 1)):
-        batch.launch(stream)
+    batch.launch(stream)
     torch.cuda.synchronize(dev)
     ms = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize(dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -610,13 +724,14 @@ def graph_bench(t, xs, tm, chunk, dev, stream, args, flush):
     nodes = batch.nodes
     batch.close()
     plan.close()
-    return {"value": len(tm) * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
-            "graph_nodes": nodes}
+    return {"value": len(tm) * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "graph_nodes": nodes, "workload": NARROW + ", the step captured once as one CUDA graph"}
 
 
-def uneven_bench(dev, stream):
+def uneven_bench(dev, stream, steps):
     """Four targets with different spans, bands and FFT lengths (2^18..2^22,
-    561..13333 templates), all in one CUDA graph; seeded noise."""
+    561..13333 templates), all in one CUDA graph; seeded noise; one
+    untimed replay, then ``steps`` timed replays."""
     import torch
 
     import paper_2201_00451_gb300 as pkg
@@ -639,13 +754,15 @@ def uneven_bench(dev, stream):
         n_tmpl += len(tm)
         n_bins += len(tm) * tg.n_fft
     batch.instantiate(stream)
+    batch.launch(stream)
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    batch.launch(stream)
+    for _ in range(steps):
+        batch.launch(stream)
     b.record(stream)
     torch.cuda.synchronize(dev)
-    ms = a.elapsed_time(b)
+    ms = a.elapsed_time(b) / steps
     nodes = batch.nodes
     batch.close()
     for p in plans:
@@ -653,48 +770,10 @@ def uneven_bench(dev, stream):
     return {"value": n_tmpl / (ms / 1e3), "unit": UNIT, "bins_per_s": n_bins / (ms / 1e3),
             "targets": [{"n_samples": tg.n_samples, "n_fft": tg.n_fft, "templates": tg.n_templates,
                          "f_het": tg.f_het} for tg in targets],
-            "ms": ms, "graph_nodes": nodes}
+            "ms_per_replay": ms, "replays": steps, "graph_nodes": nodes}
 
 
-def large_bench(dev, stream, n_tmpl=2048):
-    """The 120-day, 2^24-bin search timed on one sky position: per-sky work
-    once plus n_tmpl spindown templates, extrapolated to the full bank of
-    64 skies x 16 384 templates (per-sky work counted 64 times)."""
-    import torch
-
-    import paper_2201_00451_gb300 as pkg
-
-    t = config5()
-    xs = [make_noise(t.seed, X, t.n_samples, t.sigmas[X], "c64") for X in range(len(t.detectors))]
-    plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
-    for X in range(len(t.detectors)):
-        plan.set_data(X, xs[X], t.sigmas[X])
-    plan.autotune(stream)
-    tm = pkg.as_templates(t.templates()[:n_tmpl])
-    out = torch.empty((64, t.n_fft), dtype=torch.float32, device=dev)
-    chunks = [tm[i:i + 64] for i in range(0, len(tm), 64)]
-    plan.compute_ptr(chunks[0][:2], out.data_ptr(), stream)
-    plan.sync()
-    plan.set_profiling(True)
-    plan.invalidate_sky()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for c in chunks:
-        plan.compute_ptr(c, out.data_ptr(), stream)
-    b.record(stream)
-    plan.sync()
-    ms = a.elapsed_time(b)
-    _, ms_sky = plan.kernel_stats(2)
-    plan.close()
-    per_t = (ms - ms_sky) / len(tm)
-    total = t.n_templates
-    job_s = (len(t.skies) * ms_sky + total * per_t) / 1e3
-    return {"value": total / job_s, "unit": UNIT, "bins_per_s": total * t.n_fft / job_s,
-            "sample": f"1 sky: per-sky work {ms_sky:.2f} ms + {len(tm)} templates at {per_t * 1e3:.1f} us each",
-            "job_hours": job_s / 3600.0, "n_fft": t.n_fft, "n_samples": t.n_samples}
-
-
-def sky_heavy_bench(t, xs, dev, stream, args, n_sky=128, n_f1=11):
+def sky_heavy_bench(t, xs, dev, stream, steps, n_sky=128, n_f1=11):
     """A sky-dominated bank, shaped like the paper's pilot search (many sky
     positions, 11 spindowns each, Sec. 5.3): the 10-day two-detector data,
     128 sky positions in a 1 deg patch x 11 f1dot, per-sky work for every
@@ -712,18 +791,17 @@ def sky_heavy_bench(t, xs, dev, stream, args, n_sky=128, n_f1=11):
         plan.set_data(X, xs[X], t.sigmas[X])
     plan.autotune(stream)
     out = torch.empty((len(tm), t.n_fft), dtype=torch.float32, device=dev)
-    for _ in range(max(args.warmup, 1)):
-        plan.compute_ptr(tm, out.data_ptr(), stream)
+    plan.compute_ptr(tm, out.data_ptr(), stream)
     torch.cuda.synchronize(dev)
     plan.set_profiling(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         plan.invalidate_sky()
         plan.compute_ptr(tm, out.data_ptr(), stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    sec = e0.elapsed_time(e1) * 1e-3 / args.steps
+    sec = e0.elapsed_time(e1) * 1e-3 / steps
     n_sky_runs, ms_sky = plan.kernel_stats(2)
     plan.close()
     return {"value": len(tm) / sec, "unit": UNIT, "sky_positions_per_s": n_sky / sec,
@@ -795,7 +873,9 @@ def refine_bench(t, xs, dev, n_cand=4096, steps=20):
             "mean_2F_gain": float((hist[-1] - hist[0]).mean())}
 
 
-def e2e(t, xs, tm, chunk, dev, stream, args):
+def e2e(t, xs, tm, chunk, dev, stream, steps):
+    """The 10-day search end to end with every bin's 2F read back (550 GB
+    per step) into pinned host memory: bound by the device-to-host copy."""
     import torch
 
     import paper_2201_00451_gb300 as pkg
@@ -805,7 +885,7 @@ def e2e(t, xs, tm, chunk, dev, stream, args):
     plan = pkg.FstatPlan.from_target(t, pkg.MIXED)
     for X in range(len(t.detectors)):
         plan.set_data(X, hx[X].numpy(), t.sigmas[X])
-    set_shape(plan, args, stream)       # the autotuner's choice from its in-process cache
+    plan.autotune(stream)               # the autotuner's choice from its in-process cache
     dbuf = [torch.empty((chunk, n_fft), dtype=torch.float32, device=dev) for _ in range(2)]
     hbuf = [torch.empty((chunk, n_fft), dtype=torch.float32, pin_memory=True) for _ in range(2)]
     copy = torch.cuda.Stream(dev)
@@ -828,28 +908,26 @@ def e2e(t, xs, tm, chunk, dev, stream, args):
         copy.synchronize()
         stream.synchronize()
 
-    for _ in range(1):
-        step()
+    step()
     torch.cuda.synchronize(dev)
     s = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     torch.cuda.synchronize(dev)
     el = time.perf_counter() - s
     plan.close()
-    n = len(tm) * args.steps
-    return {"value": n / el, "unit": UNIT,
+    n = len(tm) * steps
+    return {"value": n / el, "unit": UNIT, "workload": NARROW,
             "h2d_bytes_per_step": int(sum(x.nbytes for x in xs)),
             "d2h_bytes_per_step": int(len(tm) * n_fft * 4)}
 
 
-FP32_CLOCK_MHZ = 2070.0  # maximum SM clock of the GB300 (nvidia-smi clocks.max.sm)
-PEAK_BANDS = 256         # band maxima per template (W = 16384 bins = 7.8 mHz at FFT 2^22, dt 0.5 s)
+PEAK_BANDS = 256         # band maxima per template (W = 65536 bins = 3.9 mHz at FFT 2^24, dt 1 s)
 PEAK_THRESHOLD = 70.0    # the retention threshold of Sec. 5.4
 PEAK_CAPACITY = 1 << 16
 
 
-def e2e_peaks(t, xs, tm, chunk, dev, stream, args):
+def e2e_peaks(t, xs, tm, chunk, dev, stream, args, steps):
     """End to end through fstat_compute_peaks: per step the pinned x_h go up,
     every template's 2F is reduced on the device to 256 band maxima (value
     and bin) plus the list of 2F > 70, and those come back to pinned host
@@ -907,20 +985,20 @@ def e2e_peaks(t, xs, tm, chunk, dev, stream, args):
     step()
     torch.cuda.synchronize(dev)
     s = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     torch.cuda.synchronize(dev)
     el = time.perf_counter() - s
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step(with_copies=False)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     dev_s = e0.elapsed_time(e1) * 1e-3
     n_cross = int(hcount.sum())
     plan.close()
-    n = len(tm) * args.steps
+    n = len(tm) * steps
     return {"value": n / el, "unit": UNIT,
             "h2d_bytes_per_step": int(sum(x.nbytes for x in xs)),
             "d2h_bytes_per_step": int(hmax.nbytes + hbin.nbytes + hcount.nbytes + hpeaks.nbytes),

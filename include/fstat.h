@@ -277,7 +277,8 @@ int fstat_sync(fstat_plan* plan);
 
 /* Per-kernel timing with CUDA events recorded around each launch on the
  * launching stream (off by default).  kernel: 0 = FFT pass A (spindown
- * phase + column FFTs), 1 = FFT pass B (row FFTs + 2F), 2 = per-sky work.
+ * phase + column FFTs), 1 = FFT pass B (row FFTs + 2F), 2 = per-sky work,
+ * 3 = persistent launch of both passes (fstat_set_fused).
  * fstat_kernel_stats synchronises and returns the launch count and the
  * summed event time since profiling was enabled. */
 int fstat_set_profiling(fstat_plan* plan, int enable);
@@ -319,12 +320,33 @@ int fstat_get_residency(const fstat_plan* plan, int* ra, int* rb);
  * overlap.  Synchronises. */
 int fstat_set_streams(fstat_plan* plan, int n);
 
+/* Persistent launch of the template loop (Sec. 3 template loop; the paper
+ * runs one template at a time and lists multi-template batching as future
+ * work, Sec. 6).  enable = 1: for each sky group, fstat_compute enqueues
+ * the spindown coefficients and then ONE kernel that runs both FFT passes
+ * of all the group's templates (up to 32768 per launch) as work items
+ * pulled from a queue by CTAs resident for the whole launch: pass-A tiles
+ * of template k+1 interleave with pass-B tiles of template k, a pass-B tile
+ * starts once every column of its template is done (bounded waits: a wait
+ * that runs out is FSTAT_ERR_TIMEOUT, see fstat_set_wait_limit), and three
+ * intermediates rotate.  2F and errors are as for the two-launch path;
+ * peaks mode and semi-coherent sums keep the two-launch path.  Available
+ * for FP32 plans at the splits (n1 x n2) 512x512, 512x1024, 1024x1024,
+ * 1024x2048, 1024x4096, 2048x4096 and 4096x4096; otherwise UNSUPPORTED.
+ * The autotuner (fstat_autotune) times both paths and keeps the faster.
+ * fstat_get_fused: 1 if the next fstat_compute uses it.
+ * Errors: INVALID_ARG, UNSUPPORTED. */
+int fstat_set_fused(fstat_plan* plan, int enable);
+int fstat_get_fused(const fstat_plan* plan, int* enabled);
+
 /* Polls of the first wait for each of pass B's bulk tensor copies (the
  * TMA schedules, vb bit 2): a kernel that waits longer records
  * FSTAT_ERR_TIMEOUT (returned by fstat_sync), lets its copies in flight land
  * under the full default limit, and returns.  polls < 0 restores the default
  * (2^22 polls); 0 makes every first wait give up at once, which tests of the
- * timeout path use.  Takes effect for work enqueued after the call.
+ * timeout path use.  In the persistent launch (fstat_set_fused) the limit
+ * also bounds each work item's wait for the items it depends on.  Takes
+ * effect for work enqueued after the call.
  * Errors: INVALID_ARG (NULL plan). */
 int fstat_set_wait_limit(fstat_plan* plan, int polls);
 
@@ -402,8 +424,8 @@ void fstat_batch_destroy(fstat_batch* batch);
 int fstat_probe_fma(int precision, int64_t iters, double* tflops, double* ms, void* stream);
 
 /* Kernel launches this plan has enqueued since it was created (every
- * kernel of the per-sky work, the spindown coefficients and the FFT
- * passes), for launch accounting.  Errors: INVALID_ARG. */
+ * kernel of the per-sky work, the spindown coefficients, the FFT passes and
+ * the persistent launches), for launch accounting.  Errors: INVALID_ARG. */
 int fstat_launch_count(const fstat_plan* plan, int64_t* launches);
 
 void fstat_plan_destroy(fstat_plan* plan);

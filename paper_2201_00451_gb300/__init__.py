@@ -48,7 +48,7 @@ EXPORTS = (
     "fstat_batch_launch", "fstat_batch_nodes", "fstat_batch_destroy", "fstat_set_streams",
     "fstat_compute_peaks", "fstat_semicoherent", "fstat_set_residency", "fstat_get_residency",
     "fstat_set_sfts", "fstat_export_data", "fstat_reduce_peaks", "fstat_set_wait_limit",
-    "fstat_probe_fma", "fstat_launch_count",
+    "fstat_probe_fma", "fstat_launch_count", "fstat_set_fused", "fstat_get_fused",
 )
 
 
@@ -159,6 +159,8 @@ def open_library(path: str) -> ctypes.CDLL:
         "fstat_set_wait_limit": (i32, [P, i32]),
         "fstat_probe_fma": (i32, [i32, i64, ctypes.POINTER(dbl), ctypes.POINTER(dbl), P]),
         "fstat_launch_count": (i32, [P, ctypes.POINTER(i64)]),
+        "fstat_set_fused": (i32, [P, i32]),
+        "fstat_get_fused": (i32, [P, ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -476,6 +478,18 @@ class FstatPlan:
         n = ctypes.c_int64()
         _check(self._lib.fstat_launch_count(self._p, ctypes.byref(n)), "fstat_launch_count")
         return n.value
+
+    @property
+    def fused(self) -> bool:
+        """fstat_get_fused: whether fstat_compute runs the persistent launch."""
+        v = ctypes.c_int()
+        _check(self._lib.fstat_get_fused(self._p, ctypes.byref(v)), "fstat_get_fused")
+        return bool(v.value)
+
+    def set_fused(self, enable: bool):
+        """fstat_set_fused: one persistent launch of both FFT passes per sky
+        group (raises FstatError UNSUPPORTED where no shape is compiled)."""
+        _check(self._lib.fstat_set_fused(self._p, int(bool(enable))), "fstat_set_fused")
 
     def set_wait_limit(self, polls: int):
         """fstat_set_wait_limit: polls of pass B's first bulk-copy wait per

@@ -62,7 +62,8 @@ template <> struct TwT<double> { using type = double2; };
 // 256 threads a register cap (128) that lets two CTAs share an SM; bit 3
 // (pass A, with bit 1, radix-16) = a tighter cap (80) for three CTAs per
 // SM; bit 2 (pass B) = tiles loaded by bulk tensor copies (TMA) instead of
-// per-thread 16-byte copies.  The first radix is the largest.
+// per-thread 16-byte copies; bit 2 (pass A, fused kernel only) = the
+// column staged densely by one bulk copy.  The first radix is the largest.
 __host__ __device__ constexpr bool r8(int L, int V) { return (V & 1) && L >= 1024; }
 __host__ __device__ constexpr int np_of(int L, int V) { return r8(L, V) ? 4 : (L <= 256 ? 2 : 3); }
 __host__ __device__ constexpr int r_of(int L, int p, int V) {
@@ -190,6 +191,25 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 }
 // rows per box of a pass-B tile load (the box height limit is 256)
 constexpr int kTmaRows = 256;
+// contiguous bulk copy global -> shared (16-byte aligned addresses, size a
+// multiple of 16), completion counted in bytes on the mbarrier
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// load with acquire semantics at GPU scope (a counter another CTA releases)
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// order this thread's earlier generic-proxy accesses to global memory (and
+// what it acquired) before its later async-proxy (bulk copy) accesses
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;\n" ::: "memory");
+}
 
 __device__ __forceinline__ int pad_idx(int pos, int ps) { return pos + (pos >> ps); }
 
@@ -446,6 +466,8 @@ __device__ __forceinline__ void pass_a_tile(int tile, typename PairMem<T>::type*
                                             typename PairMem<T>::type* __restrict__ Z, const F& at_free = F()) {
   using S = Shape<T, L, V>;
   using PM = typename PairMem<T>::type;
+  // staged column: padded positions (per-thread copies) or dense (one bulk copy)
+  constexpr bool kDense = (V & 4) != 0;
   const int col = tile * CA + c;
   const PM* gcol = G + (int64_t)col * lc;
   Pair<T> v[S::R0];
@@ -453,7 +475,7 @@ __device__ __forceinline__ void pass_a_tile(int tile, typename PairMem<T>::type*
     const int n2 = t + s * S::TPC;
     const int j = col + n1 * n2;
     if (j < n) {
-      Pair<T> g = STAGED ? pload(buf + pad_idx(n2, S::PS)) : pload_g(gcol + n2);
+      Pair<T> g = STAGED ? pload(buf + (kDense ? n2 : pad_idx(n2, S::PS))) : pload_g(gcol + n2);
       T cs, sn;
       spin_rot(tc, j - tc.J, &cs, &sn);
       v[s] = pmul(g, cs, sn);

@@ -89,6 +89,15 @@ struct alignas(32) TimeTab {
   double co, so, cq, sq;
 };
 
+// Per-sky timing at one node (see Geo::nodes).
+struct alignas(32) SkyNode {
+  double tm_det;  // t_m,X(t0 + j dt)
+  double v;       // (T - t0) / dt - j, T + t_m,X(T) = t_b^j
+  double a, b;    // antenna patterns at T
+};
+constexpr int kNodeStep = 16;  // samples between timing nodes
+inline int sky_nodes(int64_t n) { return (int)((n + kNodeStep - 1) / kNodeStep) + 3; }
+
 // Geometry constants for one plan (kernel argument, by value).
 struct Geo {
   double c, au, r_earth, w_rot, w_orb, cos_obl, sin_obl, orb_ph0, sid_ph0;
@@ -109,6 +118,11 @@ struct Geo {
   // Roemer delay t_m of the current sky position for each detector on the
   // same grid, [X * tab_n + i] (rewritten by every per-sky run)
   double* tm_tab;
+  // Per-sky timing nodes every kNodeStep samples (sky.cu), [X * n_nodes + m]
+  // for sample j = (m - 1) kNodeStep: t_m at the detector time, and at the
+  // SSB epoch the delay correction v = u - j and the antenna patterns a, b
+  SkyNode* nodes;
+  int n_nodes;
 };
 
 // ---------------------------------------------------- pair of complex values
@@ -254,6 +268,37 @@ inline void set_wait(PeakArgs& a, int wait_limit) {
   a.wait_set = wait_limit >= 0;
   a.wait_limit = wait_limit >= 0 ? wait_limit : 0;
 }
+// One persistent launch of both FFT passes over T templates of one sky
+// group (fft_fused.cuh).  kRing intermediates in flight; launch state of
+// queue_ints(T) ints, zeroed before every launch.
+constexpr int kRing = 3;
+constexpr int kQueueHead = 4;
+inline size_t queue_ints(int T) { return (size_t)kQueueHead + 2 * (size_t)T; }
+
+struct FusedArgs {
+  const float4* G;        // column-major resampled pairs (per-sky work)
+  int64_t lc;             // column length of G
+  int n;                  // samples
+  int n1, n2;             // split: n1 columns of n2 points (pass A), n2 rows of n1 points (pass B)
+  const TmplCoef* coef;   // [T] spindown coefficients of the launch's templates
+  const int* ord;         // [T] caller's template index of each (row = ord mod out_rows)
+  int64_t out_rows;
+  float* out;             // 2F rows of n1 * n2 floats
+  const SkyConst* sky;
+  float4* Z[kRing];       // intermediates
+  int* q;                 // launch state (queue_ints(T) ints)
+  int T;
+  int na, nb, total;      // tiles per template of pass A, of pass B; items in the launch
+  int* err;               // sticky error of the plan
+  int wait_limit;         // polls of the first waits (when wait_set), else the defaults
+  int wait_set;
+};
+
+// The fused launch for FP32 plans, compiled for the splits fused_supported
+// names (cudaErrorInvalidConfiguration otherwise).
+bool fused_supported(int log2n1, int log2n2);
+cudaError_t launch_fused_f32(int log2n1, int log2n2, const FusedArgs& a, cudaStream_t st);
+
 // Band keys of n rows x n_bands -> maximum 2F and its bin (band_bin may be null).
 cudaError_t launch_band_decode(const unsigned long long* keys, int64_t count, float* band_max,
                                int32_t* band_bin, cudaStream_t st);

@@ -65,6 +65,7 @@ struct fstat_plan {
   int nblk = 0;
   TimeTab* tab = nullptr;        // timing table (geo.tab)
   double* tm_tab = nullptr;      // per-sky Roemer delay table (geo.tm_tab)
+  SkyNode* nodes = nullptr;      // per-sky timing nodes (geo.nodes)
   SkyConst* sky = nullptr;
   void* tw = nullptr;            // twiddle tables for the current split
   TwiddleTables tt{};
@@ -95,11 +96,12 @@ struct fstat_plan {
   size_t gscratch_bytes = 0;
   cudaEvent_t cand_staged = nullptr;
   bool cand_pending = false;
-  // profiling (kernel kinds 0 = pass A, 1 = pass B, 2 = per-sky work)
+  // profiling (kernel kinds 0 = pass A, 1 = pass B, 2 = per-sky work,
+  // 3 = fused launch of both passes)
   bool prof = false;
-  std::vector<EventPair> ev[3];
+  std::vector<EventPair> ev[4];
   std::vector<EventPair> pool;
-  int64_t launches[3] = {0, 0, 0};
+  int64_t launches[4] = {0, 0, 0, 0};
   // peaks mode: band keys [templates of the call][n_bands]
   unsigned long long* keys = nullptr;
   int64_t keys_cap = 0;
@@ -109,6 +111,11 @@ struct fstat_plan {
   // polls of the first wait for a pass-B tile's bulk copies (< 0: default)
   int wait_limit = -1;
   int64_t n_launches = 0;  // kernel launches enqueued (fstat_launch_count)
+  // one persistent launch of both FFT passes per sky group and chunk of
+  // templates (FP32 plans, splits with a compiled fused shape)
+  bool fused = false;
+  int* fq = nullptr;       // launch state of the fused kernel
+  int64_t fq_cap = 0;      // templates it has room for
 };
 
 namespace {
@@ -159,6 +166,7 @@ void free_all(fstat_plan* p) {
   if (p->partials) cudaFree(p->partials);
   if (p->tab) cudaFree(p->tab);
   if (p->tm_tab) cudaFree(p->tm_tab);
+  if (p->nodes) cudaFree(p->nodes);
   if (p->sky) cudaFree(p->sky);
   if (p->tw) cudaFree(p->tw);
   if (p->d_err) cudaFree(p->d_err);
@@ -173,6 +181,7 @@ void free_all(fstat_plan* p) {
   if (p->d_cand) cudaFree(p->d_cand);
   if (p->gscratch) cudaFree(p->gscratch);
   if (p->keys) cudaFree(p->keys);
+  if (p->fq) cudaFree(p->fq);
   if (p->cand_staged) cudaEventDestroy(p->cand_staged);
   if (p->staged) cudaEventDestroy(p->staged);
   if (p->done) cudaEventDestroy(p->done);
@@ -370,9 +379,11 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   // timing table over every epoch the timing can reach: the data span
   // widened by the largest delay (|t_m| <= (au + r_earth)/c) plus margin
   {
+    // (and the timing nodes, which extend kNodeStep samples before the data
+    // and up to three node steps past it)
     const double reach = (d.ephem.au + d.ephem.r_earth) / d.ephem.c + 100.0;
-    const double lo = d.t0 - 2.0 * reach - 2.0 * kTabStep;
-    const double hi = d.t0 + (double)N * d.dt + 2.0 * reach + 2.0 * kTabStep;
+    const double lo = d.t0 - 2.0 * reach - 2.0 * kTabStep - 2.0 * kNodeStep * d.dt;
+    const double hi = d.t0 + (double)N * d.dt + 2.0 * reach + 2.0 * kTabStep + 4.0 * kNodeStep * d.dt;
     g.tab_n = time_table_entries(lo, hi, kTabStep);
     g.tab_t0 = lo;
     g.tab_inv_h = 1.0 / kTabStep;
@@ -382,6 +393,9 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
     g.tab = tab;
     if (e == cudaSuccess) e = palloc(p, &p->tm_tab, (size_t)g.tab_n * kMaxDet * sizeof(double));
     g.tm_tab = p->tm_tab;
+    g.n_nodes = sky_nodes(N);
+    if (e == cudaSuccess) e = palloc(p, &p->nodes, (size_t)g.n_nodes * d.n_det * sizeof(SkyNode));
+    g.nodes = p->nodes;
     if (e == cudaSuccess) e = launch_time_table(g, tab, 0);
   }
   if (e == cudaSuccess) e = palloc(p, &p->partials, (size_t)3 * p->nblk * sizeof(double));
@@ -523,6 +537,68 @@ int fstat_export_data(fstat_plan* p, int det, void* out, void* stream) {
 
 namespace {
 
+// Templates per fused launch (bounds the launch state and the int item count).
+constexpr int64_t kFusedMaxT = 1 << 15;
+
+bool fused_ok(const fstat_plan* p) {
+  return p->d.precision == FSTAT_MIXED && fused_supported(p->log2n1, p->log2n2);
+}
+
+// The fused launch's ring of intermediates and its launch state.
+int fused_buffers(fstat_plan* p, int64_t T) {
+  for (int r = 0; r < kRing; ++r)
+    if (!p->Zs[r]) CK(palloc(p, &p->Zs[r], (size_t)p->d.n_fft * p->pair_bytes));
+  if (T > p->fq_cap) {
+    const int64_t c = std::min<int64_t>(kFusedMaxT, std::max<int64_t>(T, 256));
+    if (p->fq) {
+      CK(cudaDeviceSynchronize());
+      cudaFree(p->fq);
+      p->fq = nullptr;
+      p->fq_cap = 0;
+    }
+    CK(palloc(p, &p->fq, queue_ints((int)c) * sizeof(int)));
+    p->fq_cap = c;
+  }
+  return FSTAT_OK;
+}
+
+// Steps (vi)-(vii) for sorted templates [i, j) of one sky group as fused
+// launches of up to kFusedMaxT templates each.
+int enqueue_fused(fstat_plan* p, int64_t i, int64_t j, const int* d_ord, const TmplCoef* d_coef, float* twoF,
+                  int64_t out_rows, cudaStream_t st, bool prof) {
+  int rc = fused_buffers(p, std::min<int64_t>(kFusedMaxT, j - i));
+  if (rc) return rc;
+  for (int64_t k0 = i; k0 < j; k0 += kFusedMaxT) {
+    const int T = (int)std::min<int64_t>(kFusedMaxT, j - k0);
+    FusedArgs a{};
+    a.G = (const float4*)p->G;
+    a.lc = p->lc;
+    a.n = (int)p->d.n_samples;
+    a.n1 = (int)p->n1;
+    a.n2 = (int)p->n2;
+    a.coef = d_coef + k0;
+    a.ord = d_ord + k0;
+    a.out_rows = out_rows;
+    a.out = twoF;
+    a.sky = p->sky;
+    for (int r = 0; r < kRing; ++r) a.Z[r] = (float4*)p->Zs[r];
+    a.q = p->fq;
+    a.T = T;
+    a.err = p->d_err;
+    a.wait_set = p->wait_limit >= 0;
+    a.wait_limit = p->wait_limit >= 0 ? p->wait_limit : 0;
+    // a.na, a.nb, a.total: filled by the launcher from its compiled shape
+    CK(cudaMemsetAsync(p->fq, 0, queue_ints(T) * sizeof(int), st));
+    EventPair e{};
+    if (prof) { e = get_events(p); cudaEventRecord(e.a, st); }
+    cudaError_t ce = launch_fused_f32(p->log2n1, p->log2n2, a, st);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    ++p->n_launches;
+    if (prof) { cudaEventRecord(e.b, st); p->ev[3].push_back(e); p->launches[3]++; }
+  }
+  return FSTAT_OK;
+}
+
 // Enqueue steps (iii)-(vii) for n templates on `st`.  h_tmpl/h_ord (host)
 // give the sky grouping; d_tmpl/d_ord/d_coef are the device copies the
 // kernels read.  force_sky: always redo the per-sky work (graph capture).
@@ -547,6 +623,12 @@ int enqueue_compute(fstat_plan* p, const fstat_template* h_tmpl, const int* h_or
     launch_tmpl_coef(p->sky, p->d.dt, p->d.n_samples, d_tmpl, d_ord, (int)i, (int)(j - i), d_coef, st);
     ++p->n_launches;
     CK(cudaGetLastError());
+    if (!po && p->fused && fused_ok(p)) {
+      int rc = enqueue_fused(p, i, j, d_ord, d_coef, twoF, out_rows, st, prof);
+      if (rc) return rc;
+      i = j;
+      continue;
+    }
     // Templates rotate over `st` and the plan's side streams, each with its
     // own intermediate, so the passes of consecutive templates overlap; the
     // side streams join back before the next sky position overwrites the
@@ -944,7 +1026,7 @@ int fstat_set_profiling(fstat_plan* p, int enable) {
 }
 
 int fstat_kernel_stats(fstat_plan* p, int kernel, int64_t* launches, double* total_ms) {
-  if (!p || kernel < 0 || kernel > 2 || !launches || !total_ms) return FSTAT_ERR_INVALID_ARG;
+  if (!p || kernel < 0 || kernel > 3 || !launches || !total_ms) return FSTAT_ERR_INVALID_ARG;
   CK(cudaDeviceSynchronize());
   double tot = 0.0;
   for (auto& e : p->ev[kernel]) {
@@ -1008,6 +1090,19 @@ int fstat_get_residency(const fstat_plan* p, int* ra, int* rb) {
   return FSTAT_OK;
 }
 
+int fstat_set_fused(fstat_plan* p, int enable) {
+  if (!p) return FSTAT_ERR_INVALID_ARG;
+  if (enable && !fused_ok(p)) return FSTAT_ERR_UNSUPPORTED;
+  p->fused = enable != 0;
+  return FSTAT_OK;
+}
+
+int fstat_get_fused(const fstat_plan* p, int* enabled) {
+  if (!p || !enabled) return FSTAT_ERR_INVALID_ARG;
+  *enabled = p->fused && fused_ok(p);
+  return FSTAT_OK;
+}
+
 int fstat_launch_count(const fstat_plan* p, int64_t* launches) {
   if (!p || !launches) return FSTAT_ERR_INVALID_ARG;
   *launches = p->n_launches;
@@ -1036,7 +1131,7 @@ int fstat_set_cta(fstat_plan* p, int ca, int va, int cb, int vb) {
 namespace {
 
 struct Choice {
-  int l1, ca, va, cb, vb;
+  int l1, ca, va, cb, vb, fused;
 };
 std::mutex g_tune_mu;
 std::map<std::string, Choice> g_tune_cache;
@@ -1046,7 +1141,7 @@ std::string tune_key(const fstat_plan* p) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) prop.name[0] = 0;
   char buf[400];
-  std::snprintf(buf, sizeof buf, "%s|N=%lld|nfft=%lld|prec=%d|ndet=%d|ns=%d", prop.name,
+  std::snprintf(buf, sizeof buf, "v2|%s|N=%lld|nfft=%lld|prec=%d|ndet=%d|ns=%d", prop.name,
                 (long long)p->d.n_samples, (long long)p->d.n_fft, p->d.precision, p->d.n_det, p->nstream);
   for (char* c = buf; *c; ++c)
     if (*c == ' ' || *c == '\t') *c = '_';
@@ -1061,7 +1156,7 @@ void load_tune_file() {
   std::ifstream in(f);
   std::string key;
   Choice c;
-  while (in >> key >> c.l1 >> c.ca >> c.va >> c.cb >> c.vb) g_tune_cache[key] = c;
+  while (in >> key >> c.l1 >> c.ca >> c.va >> c.cb >> c.vb >> c.fused) g_tune_cache[key] = c;
 }
 
 void save_tune(const std::string& key, const Choice& c) {
@@ -1069,7 +1164,7 @@ void save_tune(const std::string& key, const Choice& c) {
   const char* f = std::getenv("FSTAT_AUTOTUNE_CACHE");
   if (!f) return;
   std::ofstream out(f, std::ios::app);
-  out << key << " " << c.l1 << " " << c.ca << " " << c.va << " " << c.cb << " " << c.vb << "\n";
+  out << key << " " << c.l1 << " " << c.ca << " " << c.va << " " << c.cb << " " << c.vb << " " << c.fused << "\n";
 }
 
 // mean time (ms) of `reps` launches of pass A (which = 0) or pass B (which = 1)
@@ -1113,10 +1208,11 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
       p->va = it->second.va;
       p->cb = it->second.cb;
       p->vb = it->second.vb;
+      p->fused = it->second.fused != 0 && fused_ok(p);
       return FSTAT_OK;
     }
   }
-  const int kPipe = 16;  // templates in the overlapped pipeline timing
+  const int kPipe = 32;  // templates in the overlapped pipeline timing
   int rc = ensure_capacity(p, kPipe);
   if (rc) return rc;
   if (p->staged_pending) { CK(cudaEventSynchronize(p->staged)); p->staged_pending = false; }
@@ -1135,8 +1231,9 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int lo = std::max(kMinLog2, p->log2n - kMaxLog2), hi = std::min(kMaxLog2, p->log2n - kMinLog2);
-  Choice best{p->log2n1, 0, 0, 0, 0};
+  Choice best{p->log2n1, 0, 0, 0, 0, 0};
   float best_ms = 1e30f;
+  p->fused = false;
   static const int kCa[] = {0, 1, 2, 4};
   static const int kCb[] = {0, 1, 2, 4, 8};
   const bool saved_prof = p->prof;
@@ -1192,9 +1289,33 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
           ms = std::min(ms, t / (2 * kPipe));
         }
         if (rc) break;
-        if (ms < best_ms) { best_ms = ms; best = Choice{l1, p->ca, p->va, p->cb, p->vb}; }
+        if (ms < best_ms) { best_ms = ms; best = Choice{l1, p->ca, p->va, p->cb, p->vb, 0}; }
       }
       if (rc) break;
+    }
+    // the persistent launch of both passes over the same templates
+    if (rc == FSTAT_OK && fused_ok(p)) {
+      p->fused = true;
+      int r = enqueue_compute(p, ht.data(), ho.data(), kPipe, p->d_tmpl, p->d_order, p->d_coef, out, 1, st, false,
+                              false);
+      if (r == FSTAT_OK && cudaStreamSynchronize(st) == cudaSuccess) {
+        float ms = 1e30f;
+        for (int trial = 0; trial < 3 && rc == FSTAT_OK; ++trial) {
+          cudaEventRecord(e0, st);
+          for (int rep = 0; rep < 2; ++rep)
+            enqueue_compute(p, ht.data(), ho.data(), kPipe, p->d_tmpl, p->d_order, p->d_coef, out, 1, st, false,
+                            false);
+          cudaEventRecord(e1, st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) { rc = FSTAT_ERR_CUDA; break; }
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          ms = std::min(ms, t / (2 * kPipe));
+        }
+        if (rc == FSTAT_OK && ms < best_ms) { best_ms = ms; best = Choice{l1, p->ca, p->va, p->cb, p->vb, 1}; }
+      } else {
+        cudaGetLastError();
+      }
+      p->fused = false;
     }
   }
   p->prof = saved_prof;
@@ -1208,6 +1329,7 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
   p->va = best.va;
   p->cb = best.cb;
   p->vb = best.vb;
+  p->fused = best.fused != 0 && fused_ok(p);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   save_tune(key, best);
   return FSTAT_OK;

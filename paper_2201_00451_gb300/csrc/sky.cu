@@ -168,19 +168,67 @@ __global__ void k_sky_setup(Geo g, double alpha, double delta, SkyConst* out) {
   *out = s;
 }
 
+// Cubic Lagrange weights at f = r / kNodeStep between nodes 0 and 1 of
+// nodes at -1, 0, 1, 2 (dyadic f: every weight is exact in FP64).
+__device__ __forceinline__ void node_weights(int r, double* w) {
+  const double f = (double)r * (1.0 / kNodeStep);
+  const double fm = f - 1.0, fp = f + 1.0, f2 = f - 2.0;
+  w[0] = -f * fm * f2 * (1.0 / 6.0);
+  w[1] = fp * fm * f2 * 0.5;
+  w[2] = -fp * f * f2 * 0.5;
+  w[3] = fp * f * fm * (1.0 / 6.0);
+}
+
+// Timing nodes of the current sky position (FP64, every kNodeStep samples,
+// from sample -kNodeStep on): the Roemer delay at the detector time, and at
+// the SSB epoch t_b^j the detector epoch T (T + t_m(T) = t_b^j: the
+// fixed-point start T0 = t_b - t_m(t_b), then one Newton step; |dt_m/dT|
+// ~ 1e-4 puts T0 within ~0.05 s of the root and |d2t_m/dT2| ~ 1e-10 /s the
+// Newton step within ~1e-13 s of it, the root three fixed-point iterations
+// reach), stored as v = (T - t0)/dt - j, and the antenna patterns at T.
+// Between nodes every per-sample quantity is the cubic interpolant through
+// the four nearest nodes: t_m, T and a, b are smooth on the scale of the
+// node spacing (rotation: (w_rot h)^4 R_E/c ~ 1e-14 s at h = 32 s), so the
+// interpolation error is below the FP64 rounding of the quantities.
+__global__ void k_sky_nodes(Geo g, const SkyConst* __restrict__ skyp) {
+  const SkyConst& s = *skyp;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < g.n_nodes; m += gridDim.x * blockDim.x) {
+    const double j = (double)(m - 1) * kNodeStep;
+    const double td = g.t0 + j * g.dt;
+    const double tb = s.t_b0 + j * g.dt;
+    for (int X = 0; X < g.n_det; ++X) {
+      double T_ = tb - tm_eval(g, X, tb);
+      {
+        double dtm;
+        const double tm = tm_eval_d(g, X, T_, &dtm);
+        T_ -= (T_ + tm - tb) / (1.0 + dtm);
+      }
+      SkyNode nd;
+      nd.tm_det = tm_eval(g, X, td);
+      nd.v = (T_ - g.t0) / g.dt - j;
+      antenna(s, X, rot_eval(g, X, T_), &nd.a, &nd.b);
+      g.nodes[(int64_t)X * g.n_nodes + m] = nd;
+    }
+  }
+}
+
 // Step (iii): z = x_h exp(-i 2 pi frac(f_h t_m(t_k))), stored divided by a
 // common sigma_ref.  Rescaling every detector's series by the same factor,
 // with weights w_X = sigma_ref^2 / (2 sigma_X^2), scales G by sigma_ref and
 // A, B, C by sigma_ref^2, which leaves eq. (Fstat) unchanged while every FP32
 // value stays O(1) whatever the units of x_h (strain-scaled data would
-// overflow 1/(2 sigma^2) and |Fa|^2 in FP32).
+// overflow 1/(2 sigma^2) and |Fa|^2 in FP32).  t_m from the timing nodes.
 template <typename TIn, typename TZ>
 __global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* __restrict__ z) {
+  const SkyNode* nd = g.nodes + (int64_t)X * g.n_nodes;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < g.n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    double t = g.t0 + (double)k * g.dt;
-    double ph = g.f_het * tm_eval(g, X, t);
-    if constexpr (kNegCtrlFp32) ph = (double)((float)g.f_het * (float)tm_eval(g, X, t));
+    const int64_t m = k / kNodeStep + 1;
+    double w[4];
+    node_weights((int)(k % kNodeStep), w);
+    const double tm = w[0] * nd[m - 1].tm_det + w[1] * nd[m].tm_det + w[2] * nd[m + 1].tm_det + w[3] * nd[m + 2].tm_det;
+    double ph = g.f_het * tm;
+    if constexpr (kNegCtrlFp32) ph = (double)((float)g.f_het * (float)tm);
     ph -= floor(ph);
     TIn x = xh[k];
     const double is = g.inv_sigma_ref;
@@ -203,28 +251,21 @@ template <typename T, typename TZ>
 __global__ void __launch_bounds__(kSkyBlock)
 k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
            typename PairMem<T>::type* __restrict__ G, int n1, int64_t lc, double* __restrict__ partials) {
-  const SkyConst& s = *skyp;
+  (void)skyp;  // the sky position enters through the timing nodes
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double sa = 0.0, sb = 0.0, sab = 0.0;
   if (j < g.n) {
-    double tb = s.t_b0 + (double)j * g.dt;
+    double wn[4];
+    node_weights((int)(j % kNodeStep), wn);
     Pair<T> acc = pzero<T>();
     const int D = g.dterms;
     const T nT = (T)g.n;
     for (int X = 0; X < g.n_det; ++X) {
-      // T + t_m(T) = t_b: the fixed-point start T0 = t_b - t_m(t_b), then one
-      // Newton step.  |dt_m/dT| ~ 1e-4 puts T0 within ~0.05 s of the root and
-      // |d2t_m/dT2| ~ 1e-10 /s the Newton step within ~1e-13 s of it, below
-      // the FP64 spacing of T (~1e-10 s at 1e6 s): the root three fixed-point
-      // iterations reach, with two timing evaluations instead of four.
-      double T_ = tb - tm_eval(g, X, tb);
-      {
-        double dtm;
-        const double tm = tm_eval_d(g, X, T_, &dtm);
-        T_ -= (T_ + tm - tb) / (1.0 + dtm);
-      }
-      double u = (T_ - g.t0) / g.dt;
-      if constexpr (kNegCtrlFp32) u = (double)((float)(T_ - g.t0) / (float)g.dt);
+      // steps (iv)-(v): the sample position u of T (T + t_m(T) = t_b^j) and
+      // the antenna patterns at T, interpolated between the timing nodes
+      const SkyNode* nd = g.nodes + (int64_t)X * g.n_nodes + (j / kNodeStep + 1);
+      double u = (double)j + (wn[0] * nd[-1].v + wn[1] * nd[0].v + wn[2] * nd[1].v + wn[3] * nd[2].v);
+      if constexpr (kNegCtrlFp32) u = (double)((float)j + (float)(u - (double)j));
       long long k0 = __double2ll_rn(u);
       if (k0 < 0 || k0 > g.n - 1) continue;
       double dl = u - (double)k0;
@@ -260,8 +301,8 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
           zi += (T)v.y * wgt;
         }
       }
-      double a, b;
-      antenna(s, X, rot_eval(g, X, T_), &a, &b);
+      const double a = wn[0] * nd[-1].a + wn[1] * nd[0].a + wn[2] * nd[1].a + wn[3] * nd[2].a;
+      const double b = wn[0] * nd[-1].b + wn[1] * nd[0].b + wn[2] * nd[1].b + wn[3] * nd[2].b;
       double w = g.w[X];
       T wa = (T)(w * a), wb = (T)(w * b);
       acc.ar += wa * zr;
@@ -374,6 +415,7 @@ void launch_sky(const Geo& g, int precision, double alpha, double delta, const v
                 int n_blocks, SkyConst* sky, int* err, cudaStream_t st) {
   k_sky_setup<<<1, 32, 0, st>>>(g, alpha, delta, sky);
   k_sky_table<<<(g.tab_n + 255) / 256, 256, 0, st>>>(g, sky);
+  k_sky_nodes<<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, sky);
   for (int X = 0; X < g.n_det; ++X) {
     bool in64 = xh_dtype[X] == FSTAT_C128;
     if (precision == FSTAT_FP64) {
