@@ -472,6 +472,8 @@ def run_ours(args, rank, world, local_rank):
     leg("fp64_gpu", lambda: fp64_gpu(t, xs, tm, args.fp64_templates, dev, stream, per_gpu))
     # cuFFT (through torch.fft) for the same transforms, comparison only
     leg("cufft", lambda: cufft_bench(dev, stream, per_gpu))
+    # the radix-16 stage on CUDA cores vs as a matmul on the tensor cores
+    leg("dft16_stage", lambda: dft16_stage(dev, stream), "probe")
     # end to end through the public API: pinned host x_h -> device, every
     # bin's 2F reduced on the device (band maxima and 2F > 70, the retention
     # of Sec. 5.4), results back to pinned host memory
@@ -531,6 +533,27 @@ def cufft_bench(dev, stream, mixed_value, reps=10):
     res["note"] = ("two C2C transforms only (no spindown phase, no 2F, no zero-padding skip); the library's "
                    "whole template at 2^24 takes 1/value")
     res["ours_ms_per_template_2e24"] = 1e3 / mixed_value
+    return res
+
+
+def dft16_stage(dev, stream, blocks=1216, reps=64):
+    """The radix-16 DFT stage of the FFT passes on the CUDA cores (the
+    passes' butterflies) and as a TF32 matrix product on the tensor cores
+    (three-term split for FP32-level accuracy), same vectors, staged in
+    shared memory and transformed `reps` times: ns per 16-point vector."""
+    import torch
+
+    import paper_2201_00451_gb300 as pkg
+
+    n = 512 * blocks
+    x = torch.randn(n * 32, dtype=torch.float32, device=dev)
+    res = {}
+    for method, name in ((0, "cuda_cores"), (1, "tensor_cores_3xtf32")):
+        _, ms = pkg.probe_dft16(method, x, reps, stream)
+        res[name + "_ns_per_vector"] = ms * 1e6 / (n * reps)
+    res["tensor_over_cuda_time"] = res["tensor_cores_3xtf32_ns_per_vector"] / res["cuda_cores_ns_per_vector"]
+    res["vectors"] = n
+    res["reps"] = reps
     return res
 
 

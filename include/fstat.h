@@ -423,6 +423,24 @@ void fstat_batch_destroy(fstat_batch* batch);
  * Errors: INVALID_ARG, CUDA. */
 int fstat_probe_fma(int precision, int64_t iters, double* tflops, double* ms, void* stream);
 
+/* The radix-16 DFT stage of the FFT passes, X_m = sum_s x_s e^{-2 pi i m s/16},
+ * timed two ways on the current device (not part of the F-statistic; it
+ * measures whether the stage belongs on the tensor cores):
+ *   method 0: the passes' own butterflies on the CUDA cores (Fa, Fb pairs);
+ *   method 1: a DFT-as-matmul on the tensor cores (mma.sync TF32, operands
+ *             split into TF32 head + tail, three products: FP32-level
+ *             accuracy).
+ * `in`, `out`: DEVICE buffers of n_vectors 16-point complex FP32 vectors
+ * (n_vectors * 128 bytes, 16-byte aligned, n_vectors a multiple of 512).
+ * Layout, per 512 vectors: method 0 float4 (a.re, a.im, b.re, b.im) [s][256]
+ * (vector 2v is a of pair v, 2v + 1 its b); method 1 float [512][32] (the 16
+ * real parts, then the 16 imaginary parts).  Each 512-vector block is
+ * staged in shared memory, transformed `reps` times in place, written to
+ * `out`.  *ms: the timed launch (CUDA events, after one warm-up launch).
+ * Synchronises.  Errors: INVALID_ARG, CUDA. */
+int fstat_probe_dft16(int method, const void* in, void* out, int64_t n_vectors, int reps, double* ms,
+                      void* stream);
+
 /* Kernel launches this plan has enqueued since it was created (every
  * kernel of the per-sky work, the spindown coefficients, the FFT passes and
  * the persistent launches), for launch accounting.  Errors: INVALID_ARG. */

@@ -48,7 +48,7 @@ EXPORTS = (
     "fstat_batch_launch", "fstat_batch_nodes", "fstat_batch_destroy", "fstat_set_streams",
     "fstat_compute_peaks", "fstat_semicoherent", "fstat_set_residency", "fstat_get_residency",
     "fstat_set_sfts", "fstat_export_data", "fstat_reduce_peaks", "fstat_set_wait_limit",
-    "fstat_probe_fma", "fstat_launch_count", "fstat_set_fused", "fstat_get_fused",
+    "fstat_probe_fma", "fstat_launch_count", "fstat_set_fused", "fstat_get_fused", "fstat_probe_dft16",
 )
 
 
@@ -161,6 +161,7 @@ def open_library(path: str) -> ctypes.CDLL:
         "fstat_launch_count": (i32, [P, ctypes.POINTER(i64)]),
         "fstat_set_fused": (i32, [P, i32]),
         "fstat_get_fused": (i32, [P, ctypes.POINTER(i32)]),
+        "fstat_probe_dft16": (i32, [i32, P, P, i64, i32, ctypes.POINTER(dbl), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -507,6 +508,21 @@ def probe_fma(precision=MIXED, iters: int = 1 << 16, stream=None):
     _check(load().fstat_probe_fma(int(precision), int(iters), ctypes.byref(tf), ctypes.byref(ms),
                                   _stream_handle(stream)), "fstat_probe_fma")
     return tf.value, ms.value
+
+
+def probe_dft16(method: int, x, reps: int = 1, stream=None):
+    """fstat_probe_dft16: the radix-16 DFT stage on the CUDA cores (0) or
+    the tensor cores (1).  ``x``: CUDA tensor in the method's layout
+    (float32, n_vectors * 32 values); returns (output tensor, ms)."""
+    import torch
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    ms = ctypes.c_double()
+    n_vectors = x.numel() * x.element_size() // 128
+    _check(load().fstat_probe_dft16(int(method), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                    int(n_vectors), int(reps), ctypes.byref(ms), _stream_handle(stream)),
+           "fstat_probe_dft16")
+    return out, ms.value
 
 
 def semicoherent(plans, templates, t_ref: float, out=None, stream=None):
