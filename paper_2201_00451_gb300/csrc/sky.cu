@@ -246,73 +246,131 @@ __global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* _
   }
 }
 
-// Steps (iv) + (v) + antenna weighting + detector sum, one SSB sample per thread.
+// Steps (iv) + (v) + antenna weighting + detector sum, one SSB sample per
+// thread.  The sample positions u(j) of a block's kSkyBlock consecutive SSB
+// samples increase with j and span kSkyBlock samples give or take the
+// delay's drift, so the block stages the detector samples its taps can
+// touch, [rint(u_first) - D, rint(u_last) + D] (rounded out to float4
+// boundaries), in shared memory with coalesced 16-byte loads, and the taps
+// read them from there.  The tap weights W(d - m) use angle addition from
+// per-block tables of cos, sin(pi m / len) and of the taper's
+// cos, sin(pi m / (D + 1)), m = -D..D: two sine/cosine evaluations per
+// sample instead of two per tap.
+constexpr int kMaxD = 32;
+constexpr int kWin = kSkyBlock + 2 * kMaxD + 8;  // staged window, samples (covers the drift); even
+static_assert(kWin % 2 == 0, "whole 16-byte loads of complex64 samples");
+
 template <typename T, typename TZ>
 __global__ void __launch_bounds__(kSkyBlock)
 k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
            typename PairMem<T>::type* __restrict__ G, int n1, int64_t lc, double* __restrict__ partials) {
   (void)skyp;  // the sky position enters through the timing nodes
-  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  __shared__ __align__(16) TZ win[kWin];
+  __shared__ T tab_c[2 * kMaxD + 1], tab_s[2 * kMaxD + 1], tap_c[2 * kMaxD + 1], tap_s[2 * kMaxD + 1];
+  __shared__ long long s_span[2];
+  const int D = g.dterms;
+  const T nT = (T)g.n;
+  // Dirichlet kernel of the full series (length N) or of the 2D + 1 taps
+  // themselves; the Hamming taper only for the default kernel
+  const T len = g.interp == FSTAT_INTERP_PERIODIC ? (T)(2 * D + 1) : nT;
+  const bool taper = g.interp == FSTAT_INTERP_TAPERED;
+  const T inv_taper = (T)1 / (T)(D + 1);
+  for (int m = threadIdx.x; m <= 2 * D; m += blockDim.x) {
+    T sn, cs;
+    sincospi_t((T)(m - D) / len, &sn, &cs);
+    tab_c[m] = cs;
+    tab_s[m] = sn;
+    sincospi_t((T)(m - D) * inv_taper, &sn, &cs);
+    tap_c[m] = cs;
+    tap_s[m] = sn;
+  }
+  const int64_t j0 = (int64_t)blockIdx.x * blockDim.x;
+  int64_t j = j0 + threadIdx.x;
+  const int64_t j_last = min(j0 + (int64_t)blockDim.x, g.n) - 1;
+  double wn[4];
+  node_weights((int)(j % kNodeStep), wn);
   double sa = 0.0, sb = 0.0, sab = 0.0;
-  if (j < g.n) {
-    double wn[4];
-    node_weights((int)(j % kNodeStep), wn);
-    Pair<T> acc = pzero<T>();
-    const int D = g.dterms;
-    const T nT = (T)g.n;
-    for (int X = 0; X < g.n_det; ++X) {
-      // steps (iv)-(v): the sample position u of T (T + t_m(T) = t_b^j) and
-      // the antenna patterns at T, interpolated between the timing nodes
-      const SkyNode* nd = g.nodes + (int64_t)X * g.n_nodes + (j / kNodeStep + 1);
-      double u = (double)j + (wn[0] * nd[-1].v + wn[1] * nd[0].v + wn[2] * nd[1].v + wn[3] * nd[2].v);
-      if constexpr (kNegCtrlFp32) u = (double)((float)j + (float)(u - (double)j));
-      long long k0 = __double2ll_rn(u);
-      if (k0 < 0 || k0 > g.n - 1) continue;
-      double dl = u - (double)k0;
-      const TZ* zx = z + (int64_t)X * g.n;
-      T zr = 0, zi = 0;
-      if (dl == 0.0) {
-        TZ v = zx[k0];
-        zr = (T)v.x;
-        zi = (T)v.y;
-      } else {
-        T d = (T)dl, sd, cd_;
-        sincospi_t(d, &sd, &cd_);
-        const T inv_taper = (T)1 / (T)(D + 1);
-        // Dirichlet kernel of the full series (length N) or of the 2D + 1
-        // taps themselves; the Hamming taper only for the default kernel
-        const T len = g.interp == FSTAT_INTERP_PERIODIC ? (T)(2 * D + 1) : nT;
-        const bool taper = g.interp == FSTAT_INTERP_TAPERED;
-        for (int m = -D; m <= D; ++m) {
-          long long k = k0 + m;
-          if (k < 0 || k >= g.n) continue;
-          T x = d - (T)m;
-          T sx, cx;
-          sincospi_t(x / len, &sx, &cx);
-          T num = (m & 1) ? -sd : sd;  // sin(pi (d - m)) = (-1)^m sin(pi d)
-          T wgt = num / (len * sx);
-          if (taper) {
-            T st, ct;
-            sincospi_t(x * inv_taper, &st, &ct);
-            wgt *= (T)0.54 + (T)0.46 * ct;
+  Pair<T> acc = pzero<T>();
+  for (int X = 0; X < g.n_det; ++X) {
+    // steps (iv)-(v): the sample position u of T (T + t_m(T) = t_b^j) and
+    // the antenna patterns at T, interpolated between the timing nodes
+    const SkyNode* nd = g.nodes + (int64_t)X * g.n_nodes + (min(j, j_last) / kNodeStep + 1);
+    double u = (double)j + (wn[0] * nd[-1].v + wn[1] * nd[0].v + wn[2] * nd[1].v + wn[3] * nd[2].v);
+    if constexpr (kNegCtrlFp32) u = (double)((float)j + (float)(u - (double)j));
+    const long long k0 = __double2ll_rn(u);
+    // the block's window of detector samples (u is monotonic in j)
+    __syncthreads();  // the previous detector's window has been read
+    if (j == j0) s_span[0] = k0;
+    if (j == j_last) s_span[1] = k0;
+    __syncthreads();
+    constexpr int PER = 16 / (int)sizeof(TZ);          // samples per 16-byte load
+    // window start rounded down so that the element index X n + lo in the
+    // series buffer (16-byte aligned base) is a multiple of PER
+    long long lo = s_span[0] - D;
+    lo -= (((int64_t)X * g.n + lo) % PER + PER) % PER;
+    long long hi = s_span[1] + D;
+    if (hi - lo + 1 > kWin) hi = lo + kWin - 1;       // drift beyond the window: taps past it read global
+    const TZ* zx = z + (int64_t)X * g.n;
+    {
+      const long long n_vec = (hi - lo + PER) / PER;
+      for (long long q = threadIdx.x; q < n_vec; q += blockDim.x) {
+        const long long k = lo + q * PER;
+        if (k >= 0 && k + PER <= g.n) {
+          *reinterpret_cast<float4*>(win + q * PER) = *reinterpret_cast<const float4*>(zx + k);
+        } else {
+#pragma unroll
+          for (int e = 0; e < PER; ++e) {
+            const long long kk = k + e;
+            TZ v{};
+            if (kk >= 0 && kk < g.n) v = zx[kk];
+            win[q * PER + e] = v;
           }
-          TZ v = zx[k];
-          zr += (T)v.x * wgt;
-          zi += (T)v.y * wgt;
         }
       }
-      const double a = wn[0] * nd[-1].a + wn[1] * nd[0].a + wn[2] * nd[1].a + wn[3] * nd[2].a;
-      const double b = wn[0] * nd[-1].b + wn[1] * nd[0].b + wn[2] * nd[1].b + wn[3] * nd[2].b;
-      double w = g.w[X];
-      T wa = (T)(w * a), wb = (T)(w * b);
-      acc.ar += wa * zr;
-      acc.ai += wa * zi;
-      acc.br += wb * zr;
-      acc.bi += wb * zi;
-      sa += w * a * a;
-      sb += w * b * b;
-      sab += w * a * b;
     }
+    __syncthreads();
+    if (j >= g.n || k0 < 0 || k0 > g.n - 1) continue;
+    double dl = u - (double)k0;
+    auto tap = [&](long long k) -> TZ {
+      const long long i = k - lo;
+      return (i >= 0 && i < kWin) ? win[i] : zx[k];
+    };
+    T zr = 0, zi = 0;
+    if (dl == 0.0) {
+      TZ v = tap(k0);
+      zr = (T)v.x;
+      zi = (T)v.y;
+    } else {
+      T d = (T)dl, sd, cd_, sdl, cdl, sdt = 0, cdt = 0;
+      sincospi_t(d, &sd, &cd_);
+      sincospi_t(d / len, &sdl, &cdl);
+      if (taper) sincospi_t(d * inv_taper, &sdt, &cdt);
+      for (int m = -D; m <= D; ++m) {
+        long long k = k0 + m;
+        if (k < 0 || k >= g.n) continue;
+        // sin(pi (d - m)) = (-1)^m sin(pi d); sin(pi (d - m)/len) by angle addition
+        const T num = (m & 1) ? -sd : sd;
+        const T sx = sdl * tab_c[m + D] - cdl * tab_s[m + D];
+        T wgt = num / (len * sx);
+        if (taper) wgt *= (T)0.54 + (T)0.46 * (cdt * tap_c[m + D] + sdt * tap_s[m + D]);
+        TZ v = tap(k);
+        zr += (T)v.x * wgt;
+        zi += (T)v.y * wgt;
+      }
+    }
+    const double a = wn[0] * nd[-1].a + wn[1] * nd[0].a + wn[2] * nd[1].a + wn[3] * nd[2].a;
+    const double b = wn[0] * nd[-1].b + wn[1] * nd[0].b + wn[2] * nd[1].b + wn[3] * nd[2].b;
+    double w = g.w[X];
+    T wa = (T)(w * a), wb = (T)(w * b);
+    acc.ar += wa * zr;
+    acc.ai += wa * zi;
+    acc.br += wb * zr;
+    acc.bi += wb * zi;
+    sa += w * a * a;
+    sb += w * b * b;
+    sab += w * a * b;
+  }
+  if (j < g.n) {
     int64_t n1i = j % n1, n2i = j / n1;
     pstore(G + n1i * lc + n2i, acc);
   }
