@@ -152,17 +152,18 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, length: int, c: int, v: int):
+def ncu_traffic(kernel: str, length: int, c: int, v: int, workload: str):
     """DRAM bytes per launch of one pass shape (FFT length, columns or rows
-    per CTA, radix schedule) from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    per CTA, radix schedule) on one workload ("large" or "narrow") from the
+    committed ncu summary, if it was taken on the current kernel source
+    (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         if t.get("source_hash") != kernel_source_hash():
             return None
         for e in t["entries"]:
-            if (e["kernel"], e["L"], e["c"], e["v"]) == (kernel, length, c, v):
+            if (e["kernel"], e["L"], e["c"], e["v"], e.get("workload")) == (kernel, length, c, v, workload):
                 return float(e["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError, TypeError):
         pass
@@ -323,7 +324,8 @@ def serial_roofline(plan, t, tm, out, stream, n=32):
     return res
 
 
-def roofline_line(serial, t, value_per_gpu, hbm_peak, peak_kind, f32_peak, f32_kind, plan, ms_per_template):
+def roofline_line(serial, t, value_per_gpu, hbm_peak, peak_kind, f32_peak, f32_kind, plan, ms_per_template,
+                  workload):
     dom = max(serial, key=lambda k: serial[k][1])
     nl, tot, bytes_alg = serial[dom]
     avg_s = tot / 1e3 / nl
@@ -335,7 +337,7 @@ def roofline_line(serial, t, value_per_gpu, hbm_peak, peak_kind, f32_peak, f32_k
     flops_t = 2 * 5 * t.n_fft * math.log2(t.n_fft)
     serial_ms = sum(v[1] / v[0] for k, v in serial.items() if k in (0, 1))
     return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": ncu_traffic(PASS_BYTES[dom], *shape),
+            "frac": achieved / hbm_peak, "traffic": ncu_traffic(PASS_BYTES[dom], *shape, workload),
             "kernel": PASS_BYTES[dom], "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy)",
             "timing": f"serialised pass: one template stream, {nl} launches, CUDA events per launch",
             "kernel_ms_per_launch": avg_s * 1e3, "bytes_per_launch": bytes_alg,
@@ -436,7 +438,7 @@ def run_ours(args, rank, world, local_rank):
                           (torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2 * 2.07e9 / 1e12,
                            "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz"))
     roof = roofline_line(serial, t, per_gpu, hbm_peak, peak_kind, f32_peak, f32_kind, plan,
-                         ms / args.steps / n_tmpl)
+                         ms / args.steps / n_tmpl, "large")
     split, cta = plan.split, plan.cta
     plan.close()
     del out
@@ -592,7 +594,8 @@ def narrow_bench(t, xs, tm, dev, stream, args, steps, flush, hbm_peak, peak_kind
         ms += a.elapsed_time(b)
     value = len(tm) * steps / (ms / 1e3)
     serial = serial_roofline(plan, t, tm, out, stream)
-    roof = roofline_line(serial, t, value, hbm_peak, peak_kind, f32_peak, f32_kind, plan, ms / steps / len(tm))
+    roof = roofline_line(serial, t, value, hbm_peak, peak_kind, f32_peak, f32_kind, plan, ms / steps / len(tm),
+                         "narrow")
     plan.close()
     return {"value": value, "unit": UNIT, "bins_per_s": value * t.n_fft, "ms_per_step": ms / steps,
             "workload": NARROW, "roofline": roof}
