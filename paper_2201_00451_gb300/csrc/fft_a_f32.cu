@@ -23,6 +23,7 @@ template <typename T> int default_c_len(int log2_len, bool pass_b) {
     case 10: return default_c<T, 1024>(pass_b);
     case 11: return default_c<T, 2048>(pass_b);
     case 12: return default_c<T, 4096>(pass_b);
+    case 13: return pass_b ? 0 : 1;  // 8192-point columns: one per CTA
     default: return 0;
   }
 }

@@ -65,9 +65,11 @@ template <> struct TwT<double> { using type = double2; };
 // per-thread 16-byte copies; bit 2 (pass A, fused kernel only) = the
 // column staged densely by one bulk copy.  The first radix is the largest.
 __host__ __device__ constexpr bool r8(int L, int V) { return (V & 1) && L >= 1024; }
-__host__ __device__ constexpr int np_of(int L, int V) { return r8(L, V) ? 4 : (L <= 256 ? 2 : 3); }
+__host__ __device__ constexpr int np_of(int L, int V) {
+  return r8(L, V) ? (L == 8192 ? 5 : 4) : (L <= 256 ? 2 : (L <= 4096 ? 3 : 4));
+}
 __host__ __device__ constexpr int r_of(int L, int p, int V) {
-  return r8(L, V)   ? (p < 3 ? 8 : L / 512)
+  return r8(L, V)   ? (L == 8192 ? (p < 4 ? 8 : 2) : (p < 3 ? 8 : L / 512))
        : L == 32    ? (p == 0 ? 8 : 4)
        : L == 64    ? 8
        : L == 128   ? (p == 0 ? 16 : 8)
@@ -75,12 +77,18 @@ __host__ __device__ constexpr int r_of(int L, int p, int V) {
        : L == 512   ? 8
        : L == 1024  ? (p == 0 ? 16 : 8)
        : L == 2048  ? (p == 2 ? 8 : 16)
+       : L == 8192  ? (p == 3 ? 2 : 16)  // pass A only: 16 x 16 x 16 x 2
        : 16;  // 4096
 }
 __host__ __device__ constexpr int ns_of(int L, int p, int V) {
   return p == 0 ? 1 : ns_of(L, p - 1, V) * r_of(L, p - 1, V);
 }
 __host__ __device__ constexpr int log2c(int x) { return x <= 1 ? 0 : 1 + log2c(x / 2); }
+
+// product of the schedule's radices (must be L)
+__host__ __device__ constexpr int radix_product(int L, int V, int p = 0) {
+  return p == np_of(L, V) ? 1 : r_of(L, p, V) * radix_product(L, V, p + 1);
+}
 
 template <typename T, int L, int V = 0> struct Shape {
   static constexpr int NP = np_of(L, V);
@@ -95,6 +103,11 @@ template <typename T, int L, int V = 0> struct Shape {
   static constexpr int CB_DEF = TPC >= 128 ? CB_MIN : (128 / TPC > CB_MIN ? 128 / TPC : CB_MIN);
   using PM = typename PairMem<T>::type;
   using TW = typename TwT<T>::type;
+  // every pass's radix divides the points per thread (each thread owns whole
+  // butterflies of every pass, the last one included) and the radices
+  // multiply to L
+  static_assert(radix_product(L, V) == L, "radix schedule does not multiply to the length");
+  static_assert(R0 % RL == 0 && R0 >= RL, "the last pass's butterflies do not cover the points of a thread");
 };
 
 // Shared memory of a persistent pass kernel: NBUF padded buffers of C
@@ -1130,12 +1143,21 @@ cudaError_t pick_b(int cb, int v, const void* Z, int n2, const void* twB, const 
   case 11: return F<T, 2048 __VA_ARGS__; \
   case 12: return F<T, 4096 __VA_ARGS__;
 
+// 8192-point columns (FP32 only: one padded column of FP64 pairs would not
+// fit shared memory), compiled in a translation unit of their own
+cudaError_t pick_a_8192(int ca, int v, const void* G, int64_t lc, int64_t n, int n1, const void* twA,
+                        const void* hi, const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st,
+                        int res);
+
 template <typename T>
 cudaError_t dispatch_a(int log2_n2, int ca, int v, const void* G, int64_t lc, int64_t n, int n1, const void* twA,
                        const void* hi, const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st,
                        int res = 0) {
   switch (log2_n2) {
     FSTAT_LEN_CASES(pick_a, >(ca, v, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res))
+    case 13:
+      if constexpr (sizeof(T) == 4) return pick_a_8192(ca, v, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

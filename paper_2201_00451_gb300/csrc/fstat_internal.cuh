@@ -12,8 +12,9 @@ namespace fstat {
 // ---------------------------------------------------------------- constants
 constexpr int kMaxDet = FSTAT_MAX_DET;
 constexpr int kSkyBlock = 256;      // threads per block of the per-SSB-sample kernel
-constexpr int kMinLog2 = 5;         // FFT pass lengths 32 .. 4096
+constexpr int kMinLog2 = 5;         // FFT pass lengths 32 .. 4096 (pass B rows)
 constexpr int kMaxLog2 = 12;
+constexpr int kMaxLog2A = 13;       // pass A columns up to 8192 (FP32 plans)
 
 // Per-sky constants, written by k_sky_setup / k_sky_finalize (device memory).
 struct SkyConst {

@@ -237,7 +237,8 @@ int run_sky(fstat_plan* p, double alpha, double delta, cudaStream_t st) {
 
 int set_split(fstat_plan* p, int log2n1) {
   int log2n2 = p->log2n - log2n1;
-  if (log2n1 < kMinLog2 || log2n1 > kMaxLog2 || log2n2 < kMinLog2 || log2n2 > kMaxLog2)
+  const int max2 = p->d.precision == FSTAT_FP64 ? kMaxLog2 : kMaxLog2A;
+  if (log2n1 < kMinLog2 || log2n1 > kMaxLog2 || log2n2 < kMinLog2 || log2n2 > max2)
     return FSTAT_ERR_UNSUPPORTED;
   p->log2n1 = log2n1;
   p->log2n2 = log2n2;
@@ -400,7 +401,7 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
   }
   if (e == cudaSuccess) e = palloc(p, &p->partials, (size_t)3 * p->nblk * sizeof(double));
   if (e == cudaSuccess) e = palloc(p, &p->sky, sizeof(SkyConst));
-  if (e == cudaSuccess) e = palloc(p, &p->tw, (size_t)4 * (size_t(1) << kMaxLog2) * 16);
+  if (e == cudaSuccess) e = palloc(p, &p->tw, (size_t)4 * (size_t(1) << kMaxLog2A) * 16);
   if (e == cudaSuccess) e = palloc(p, &p->d_err, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_err, 2 * sizeof(int));
@@ -1230,7 +1231,8 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int lo = std::max(kMinLog2, p->log2n - kMaxLog2), hi = std::min(kMaxLog2, p->log2n - kMinLog2);
+  const int max2 = p->d.precision == FSTAT_FP64 ? kMaxLog2 : kMaxLog2A;
+  const int lo = std::max(kMinLog2, p->log2n - max2), hi = std::min(kMaxLog2, p->log2n - kMinLog2);
   Choice best{p->log2n1, 0, 0, 0, 0, 0};
   float best_ms = 1e30f;
   p->fused = false;
