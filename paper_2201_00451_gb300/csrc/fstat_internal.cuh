@@ -123,6 +123,7 @@ struct Geo {
   // for sample j = (m - 1) kNodeStep: t_m at the detector time, and at the
   // SSB epoch the delay correction v = u - j and the antenna patterns a, b
   SkyNode* nodes;
+  float2* nodes_ab32;                  // (a, b) at the same nodes in FP32 (for G)
   int n_nodes;
 };
 

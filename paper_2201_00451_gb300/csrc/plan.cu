@@ -66,6 +66,7 @@ struct fstat_plan {
   TimeTab* tab = nullptr;        // timing table (geo.tab)
   double* tm_tab = nullptr;      // per-sky Roemer delay table (geo.tm_tab)
   SkyNode* nodes = nullptr;      // per-sky timing nodes (geo.nodes)
+  float2* nodes_ab32 = nullptr;  // their antenna patterns in FP32 (geo.nodes_ab32)
   SkyConst* sky = nullptr;
   void* tw = nullptr;            // twiddle tables for the current split
   TwiddleTables tt{};
@@ -167,6 +168,7 @@ void free_all(fstat_plan* p) {
   if (p->tab) cudaFree(p->tab);
   if (p->tm_tab) cudaFree(p->tm_tab);
   if (p->nodes) cudaFree(p->nodes);
+  if (p->nodes_ab32) cudaFree(p->nodes_ab32);
   if (p->sky) cudaFree(p->sky);
   if (p->tw) cudaFree(p->tw);
   if (p->d_err) cudaFree(p->d_err);
@@ -396,7 +398,9 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
     g.tm_tab = p->tm_tab;
     g.n_nodes = sky_nodes(N);
     if (e == cudaSuccess) e = palloc(p, &p->nodes, (size_t)g.n_nodes * d.n_det * sizeof(SkyNode));
+    if (e == cudaSuccess) e = palloc(p, &p->nodes_ab32, (size_t)g.n_nodes * d.n_det * sizeof(float2));
     g.nodes = p->nodes;
+    g.nodes_ab32 = p->nodes_ab32;
     if (e == cudaSuccess) e = launch_time_table(g, tab, 0);
   }
   if (e == cudaSuccess) e = palloc(p, &p->partials, (size_t)3 * p->nblk * sizeof(double));

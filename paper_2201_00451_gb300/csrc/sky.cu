@@ -208,6 +208,7 @@ __global__ void k_sky_nodes(Geo g, const SkyConst* __restrict__ skyp) {
       nd.v = (T_ - g.t0) / g.dt - j;
       antenna(s, X, rot_eval(g, X, T_), &nd.a, &nd.b);
       g.nodes[(int64_t)X * g.n_nodes + m] = nd;
+      g.nodes_ab32[(int64_t)X * g.n_nodes + m] = make_float2((float)nd.a, (float)nd.b);
     }
   }
 }
@@ -220,12 +221,14 @@ __global__ void k_sky_nodes(Geo g, const SkyConst* __restrict__ skyp) {
 // overflow 1/(2 sigma^2) and |Fa|^2 in FP32).  t_m from the timing nodes.
 template <typename TIn, typename TZ>
 __global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* __restrict__ z) {
+  __shared__ double s_w[kNodeStep][4];  // the node weights, by sample mod kNodeStep
+  if (threadIdx.x < kNodeStep) node_weights(threadIdx.x, s_w[threadIdx.x]);
+  __syncthreads();
   const SkyNode* nd = g.nodes + (int64_t)X * g.n_nodes;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < g.n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t m = k / kNodeStep + 1;
-    double w[4];
-    node_weights((int)(k % kNodeStep), w);
+    const double* w = s_w[k % kNodeStep];
     const double tm = w[0] * nd[m - 1].tm_det + w[1] * nd[m].tm_det + w[2] * nd[m + 1].tm_det + w[3] * nd[m + 2].tm_det;
     double ph = g.f_het * tm;
     if constexpr (kNegCtrlFp32) ph = (double)((float)g.f_het * (float)tm);
@@ -256,6 +259,16 @@ __global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* _
 // per-block tables of cos, sin(pi m / len) and of the taper's
 // cos, sin(pi m / (D + 1)), m = -D..D: two sine/cosine evaluations per
 // sample instead of two per tap.
+//
+// FP64 work per sample is kept to what needs it: u (the sample position,
+// from the nodes' v) in FP64; a, b for the weighted sum G in FP32 from FP32
+// copies of the node values (G itself is FP32; the FP64 path keeps FP64);
+// and A, B, C per 16-sample segment: with a(r) = sum_q W_rq a_q the cubic
+// interpolant of the segment's four node values a_q, the segment's
+// sum_r a(r)^2 is the quadratic form a^T M a with M = sum_r W_r W_r^T
+// (and likewise b^T M b, a^T M b), exact algebra in FP64, one thread per
+// detector and segment after the sample loop; segments with invalid
+// samples (the data's edges) sum per sample.
 constexpr int kMaxD = 32;
 constexpr int kWin = kSkyBlock + 2 * kMaxD + 8;  // staged window, samples (covers the drift); even
 static_assert(kWin % 2 == 0, "whole 16-byte loads of complex64 samples");
@@ -268,6 +281,11 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
   __shared__ __align__(16) TZ win[kWin];
   __shared__ T tab_c[2 * kMaxD + 1], tab_s[2 * kMaxD + 1], tap_c[2 * kMaxD + 1], tap_s[2 * kMaxD + 1];
   __shared__ long long s_span[2];
+  __shared__ double s_w[kNodeStep][4], s_m[4][4];  // node weights by j mod kNodeStep; segment matrix M
+  __shared__ float s_wf[kNodeStep][4];
+  __shared__ bool s_full[kMaxDet][kSkyBlock / kNodeStep];  // segment fully valid, per detector
+  static_assert(kSkyBlock % 32 == 0 && kNodeStep == 16, "two whole segments per warp");
+  static_assert(kMaxDet * (kSkyBlock / kNodeStep) <= kSkyBlock, "one thread per detector and segment");
   const int D = g.dterms;
   const T nT = (T)g.n;
   // Dirichlet kernel of the full series (length N) or of the 2D + 1 taps
@@ -284,17 +302,31 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
     tap_c[m] = cs;
     tap_s[m] = sn;
   }
+  if (threadIdx.x < kNodeStep) {
+    node_weights(threadIdx.x, s_w[threadIdx.x]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s_wf[threadIdx.x][q] = (float)s_w[threadIdx.x][q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    const int q = threadIdx.x >> 2, r2 = threadIdx.x & 3;
+    double m = 0.0;
+    for (int r = 0; r < kNodeStep; ++r) m += s_w[r][q] * s_w[r][r2];
+    s_m[q][r2] = m;  // visible after the barriers in the detector loop
+  }
   const int64_t j0 = (int64_t)blockIdx.x * blockDim.x;
   int64_t j = j0 + threadIdx.x;
   const int64_t j_last = min(j0 + (int64_t)blockDim.x, g.n) - 1;
-  double wn[4];
-  node_weights((int)(j % kNodeStep), wn);
+  const double* wn = s_w[j % kNodeStep];
+  const float* wf = s_wf[j % kNodeStep];
+  const unsigned lane = threadIdx.x & 31;
   double sa = 0.0, sb = 0.0, sab = 0.0;
   Pair<T> acc = pzero<T>();
   for (int X = 0; X < g.n_det; ++X) {
     // steps (iv)-(v): the sample position u of T (T + t_m(T) = t_b^j) and
     // the antenna patterns at T, interpolated between the timing nodes
-    const SkyNode* nd = g.nodes + (int64_t)X * g.n_nodes + (min(j, j_last) / kNodeStep + 1);
+    const int64_t node0 = (int64_t)X * g.n_nodes + (min(j, j_last) / kNodeStep + 1);
+    const SkyNode* nd = g.nodes + node0;
     double u = (double)j + (wn[0] * nd[-1].v + wn[1] * nd[0].v + wn[2] * nd[1].v + wn[3] * nd[2].v);
     if constexpr (kNegCtrlFp32) u = (double)((float)j + (float)(u - (double)j));
     const long long k0 = __double2ll_rn(u);
@@ -329,7 +361,21 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
       }
     }
     __syncthreads();
-    if (j >= g.n || k0 < 0 || k0 > g.n - 1) continue;
+    // A, B, C: fully valid 16-sample segments are summed after this loop
+    // (one thread per detector and segment); the others per sample here
+    const bool valid = j < g.n && k0 >= 0 && k0 <= g.n - 1;
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    const bool seg_full = ((vmask >> (lane & 16u)) & 0xffffu) == 0xffffu;
+    if ((lane & 15u) == 0) s_full[X][threadIdx.x / kNodeStep] = seg_full;
+    const double w = g.w[X];
+    if (!seg_full && valid) {
+      const double a = wn[0] * nd[-1].a + wn[1] * nd[0].a + wn[2] * nd[1].a + wn[3] * nd[2].a;
+      const double b = wn[0] * nd[-1].b + wn[1] * nd[0].b + wn[2] * nd[1].b + wn[3] * nd[2].b;
+      sa += w * a * a;
+      sb += w * b * b;
+      sab += w * a * b;
+    }
+    if (!valid) continue;
     double dl = u - (double)k0;
     auto tap = [&](long long k) -> TZ {
       const long long i = k - lo;
@@ -358,21 +404,59 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
         zi += (T)v.y * wgt;
       }
     }
-    const double a = wn[0] * nd[-1].a + wn[1] * nd[0].a + wn[2] * nd[1].a + wn[3] * nd[2].a;
-    const double b = wn[0] * nd[-1].b + wn[1] * nd[0].b + wn[2] * nd[1].b + wn[3] * nd[2].b;
-    double w = g.w[X];
-    T wa = (T)(w * a), wb = (T)(w * b);
+    // the antenna-weighted detector sum G (FP32 a, b in the mixed path)
+    T wa, wb;
+    if constexpr (sizeof(T) == sizeof(float)) {
+      const float2* ab = g.nodes_ab32 + node0;
+      const float a = wf[0] * ab[-1].x + wf[1] * ab[0].x + wf[2] * ab[1].x + wf[3] * ab[2].x;
+      const float b = wf[0] * ab[-1].y + wf[1] * ab[0].y + wf[2] * ab[1].y + wf[3] * ab[2].y;
+      const float wx = (float)w;
+      wa = wx * a;
+      wb = wx * b;
+    } else {
+      const double a = wn[0] * nd[-1].a + wn[1] * nd[0].a + wn[2] * nd[1].a + wn[3] * nd[2].a;
+      const double b = wn[0] * nd[-1].b + wn[1] * nd[0].b + wn[2] * nd[1].b + wn[3] * nd[2].b;
+      wa = (T)(w * a);
+      wb = (T)(w * b);
+    }
     acc.ar += wa * zr;
     acc.ai += wa * zi;
     acc.br += wb * zr;
     acc.bi += wb * zi;
-    sa += w * a * a;
-    sb += w * b * b;
-    sab += w * a * b;
   }
   if (j < g.n) {
     int64_t n1i = j % n1, n2i = j / n1;
     pstore(G + n1i * lc + n2i, acc);
+  }
+  // the fully valid segments' A, B, C: sum_r a(r)^2 over a segment = a^T M a
+  // in the four node values (likewise b^T M b, a^T M b), one thread per
+  // detector and segment, all lanes of a warp busy
+  __syncthreads();
+  constexpr int kSeg = kSkyBlock / kNodeStep;
+  if (threadIdx.x < g.n_det * kSeg) {
+    const int X = threadIdx.x / kSeg, sg = threadIdx.x % kSeg;
+    if (s_full[X][sg]) {
+      const SkyNode* nd = g.nodes + (int64_t)X * g.n_nodes + (j0 / kNodeStep + sg + 1);
+      const double av[4] = {nd[-1].a, nd[0].a, nd[1].a, nd[2].a};
+      const double bv[4] = {nd[-1].b, nd[0].b, nd[1].b, nd[2].b};
+      double aMa = 0.0, bMb = 0.0, aMb = 0.0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double ma = 0.0, mb = 0.0;
+#pragma unroll
+        for (int r2 = 0; r2 < 4; ++r2) {
+          ma += s_m[q][r2] * av[r2];
+          mb += s_m[q][r2] * bv[r2];
+        }
+        aMa += av[q] * ma;
+        bMb += bv[q] * mb;
+        aMb += av[q] * mb;
+      }
+      const double w = g.w[X];
+      sa += w * aMa;
+      sb += w * bMb;
+      sab += w * aMb;
+    }
   }
   // block reduction of the A, B, C partial sums (fixed order)
   __shared__ double red[3][kSkyBlock / 32];
@@ -381,7 +465,7 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
     sb += __shfl_down_sync(0xffffffffu, sb, o);
     sab += __shfl_down_sync(0xffffffffu, sab, o);
   }
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int wid = threadIdx.x >> 5;
   if (lane == 0) { red[0][wid] = sa; red[1][wid] = sb; red[2][wid] = sab; }
   __syncthreads();
   if (threadIdx.x == 0) {
