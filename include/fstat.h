@@ -300,7 +300,12 @@ int fstat_set_split(fstat_plan* plan, int64_t n1);
  * only: bit 2 = pass B tile loads by the tensor-memory-access engine
  * (FP32, rows of 1024 points or more; a load that does not complete within
  * a bounded wait ends the kernel, and fstat_sync() then returns
- * FSTAT_ERR_TIMEOUT).  va 0..3 or 10, vb 0..7.  A shape that is not
+ * FSTAT_ERR_TIMEOUT); va 16 (FP32, 8192-point columns, one per CTA) =
+ * the next column's samples copied by one bulk copy into shared memory of
+ * their own while the current column is transformed (the plan's samples
+ * per column must fit beside the column buffer; a copy that does not
+ * complete within a bounded wait likewise gives FSTAT_ERR_TIMEOUT).  va
+ * 0..3, 10 or 16, vb 0..7.  A shape that is not
  * compiled for the current split makes fstat_compute return
  * FSTAT_ERR_CUDA.  fstat_get_cta reports the shapes in effect (a default
  * as its value for the current split). */
@@ -340,7 +345,8 @@ int fstat_set_fused(fstat_plan* plan, int enable);
 int fstat_get_fused(const fstat_plan* plan, int* enabled);
 
 /* Polls of the first wait for each of pass B's bulk tensor copies (the
- * TMA schedules, vb bit 2): a kernel that waits longer records
+ * TMA schedules, vb bit 2) and of the wait for each staged column of pass
+ * A's schedule 16: a kernel that waits longer records
  * FSTAT_ERR_TIMEOUT (returned by fstat_sync), lets its copies in flight land
  * under the full default limit, and returns.  polls < 0 restores the default
  * (2^22 polls); 0 makes every first wait give up at once, which tests of the

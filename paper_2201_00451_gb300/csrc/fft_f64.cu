@@ -4,9 +4,9 @@
 namespace fstat {
 
 cudaError_t launch_pass_a_f64(int log2_n2, int ca, int va, const void* G, int64_t lc, int64_t n, int n1,
-                              const void* twA, const void* hi, const void* lo, int h, const TmplCoef* coef,
-                              void* Z, cudaStream_t st, int res) {
-  return fft::dispatch_a<double>(log2_n2, ca, va, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
+                              const void* twA, const TmplCoef* coef, void* Z, cudaStream_t st, int res, int* err,
+                              int wait_limit) {
+  return fft::dispatch_a<double>(log2_n2, ca, va, G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res);
 }
 
 cudaError_t launch_pass_b_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,

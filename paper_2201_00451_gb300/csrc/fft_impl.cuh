@@ -63,7 +63,10 @@ template <> struct TwT<double> { using type = double2; };
 // (pass A, with bit 1, radix-16) = a tighter cap (80) for three CTAs per
 // SM; bit 2 (pass B) = tiles loaded by bulk tensor copies (TMA) instead of
 // per-thread 16-byte copies; bit 2 (pass A, fused kernel only) = the
-// column staged densely by one bulk copy.  The first radix is the largest.
+// column staged densely by one bulk copy; bit 4 (pass A, 8192-point
+// columns) = the next column's samples copied densely by one bulk copy into
+// a staging area of their own while this column is transformed.  The first
+// radix is the largest.
 __host__ __device__ constexpr bool r8(int L, int V) { return (V & 1) && L >= 1024; }
 __host__ __device__ constexpr int np_of(int L, int V) {
   return r8(L, V) ? (L == 8192 ? 5 : 4) : (L <= 256 ? 2 : (L <= 4096 ? 3 : 4));
@@ -116,7 +119,7 @@ template <typename T, int L, int V = 0> struct Shape {
 constexpr size_t kSmemCap = (size_t)220 * 1024;
 template <typename T, int L, int C, int V = 0> struct Buf {
   static constexpr size_t ONE = (size_t)C * Shape<T, L, V>::LP * sizeof(typename Shape<T, L, V>::PM);
-  static constexpr int NBUF = (kPipeline && !(V & 2) && 2 * ONE <= kSmemCap) ? 2 : 1;
+  static constexpr int NBUF = (kPipeline && !(V & 2) && !(V & 16) && 2 * ONE <= kSmemCap) ? 2 : 1;
   static constexpr size_t BYTES = NBUF * ONE;
 };
 
@@ -469,18 +472,24 @@ __device__ __forceinline__ void spin_rot(const TmplCoef& c, int si, double* cs, 
 
 // ------------------------------------------------------------- pass A
 // One tile = CA columns.  `staged`: the column samples were copied to `buf`
-// (at padded natural positions) by cp.async; otherwise they are loaded from
-// global memory straight into registers.
-template <typename T, int L, int CA, int V, bool STAGED, typename F = NoOp>
+// (at padded natural positions) by cp.async, or densely (one bulk copy) to
+// `buf` or, with schedule bit 4, to the separate area `stg`; otherwise they
+// are loaded from global memory straight into registers.  at_staged() runs
+// once every thread has read `stg` (after the barrier that ends the first
+// pass's stores).
+template <typename T, int L, int CA, int V, bool STAGED, typename F = NoOp, typename H = NoOp>
 __device__ __forceinline__ void pass_a_tile(int tile, typename PairMem<T>::type* buf, int c, int t,
                                             const typename PairMem<T>::type* __restrict__ G, int64_t lc,
                                             int n, int n1, const typename TwT<T>::type* __restrict__ twL,
                                             const TmplCoef& tc, T inv_n,
-                                            typename PairMem<T>::type* __restrict__ Z, const F& at_free = F()) {
+                                            typename PairMem<T>::type* __restrict__ Z, const F& at_free = F(),
+                                            const typename PairMem<T>::type* stg = nullptr,
+                                            const H& at_staged = H()) {
   using S = Shape<T, L, V>;
   using PM = typename PairMem<T>::type;
   // staged column: padded positions (per-thread copies) or dense (one bulk copy)
-  constexpr bool kDense = (V & 4) != 0;
+  constexpr bool kSep = (V & 16) != 0;
+  constexpr bool kDense = (V & 4) != 0 || kSep;
   const int col = tile * CA + c;
   const PM* gcol = G + (int64_t)col * lc;
   Pair<T> v[S::R0];
@@ -488,7 +497,7 @@ __device__ __forceinline__ void pass_a_tile(int tile, typename PairMem<T>::type*
     const int n2 = t + s * S::TPC;
     const int j = col + n1 * n2;
     if (j < n) {
-      Pair<T> g = STAGED ? pload(buf + (kDense ? n2 : pad_idx(n2, S::PS))) : pload_g(gcol + n2);
+      Pair<T> g = STAGED ? pload(kSep ? stg + n2 : buf + (kDense ? n2 : pad_idx(n2, S::PS))) : pload_g(gcol + n2);
       T cs, sn;
       spin_rot(tc, j - tc.J, &cs, &sn);
       v[s] = pmul(g, cs, sn);
@@ -506,10 +515,11 @@ __device__ __forceinline__ void pass_a_tile(int tile, typename PairMem<T>::type*
 #pragma unroll
     for (int s = 0; s < S::R0; ++s) load(s);
   }
-  if constexpr (STAGED) __syncthreads();  // the staged column is overwritten below
+  if constexpr (STAGED && !kSep) __syncthreads();  // the staged column is overwritten below
   if (half) dft_half<T, S::R0>(v);
   else dft<T, S::R0>(v);
   store_pass0<T, L, V, 1>(v, buf, t);
+  at_staged();
   passes<T, L, V, 1, 1, false, F>(v, buf, t, twL, at_free);
 
   // four-step twiddle W_N^{col k2} = W_N^{col b} (W_N^{col NSL})^s for
@@ -553,7 +563,7 @@ template <typename T, int L, int CA, int V>
 __global__ void __launch_bounds__(CA * Shape<T, L, V>::TPC, (min_blocks<T, L, CA, V>()))
 k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int n1,
          const typename TwT<T>::type* __restrict__ twL, const TmplCoef* __restrict__ coefp,
-         typename PairMem<T>::type* __restrict__ Z) {
+         typename PairMem<T>::type* __restrict__ Z, int* __restrict__ err, int wait_limit) {
   using S = Shape<T, L, V>;
   using B = Buf<T, L, CA, V>;
   using PM = typename PairMem<T>::type;
@@ -566,6 +576,56 @@ k_pass_a(const typename PairMem<T>::type* __restrict__ G, int64_t lc, int n, int
   const T inv_n = (T)1 / (T)(1 << log2N);
   if constexpr (!kPipeline) {
     pass_a_tile<T, L, CA, V, false>(blockIdx.x, smem + c * S::LP, c, t, G, lc, n, n1, twL, tc, inv_n, Z);
+  } else if constexpr ((V & 16) != 0) {
+    // Input double-buffered: thread 0 copies the next column's samples
+    // (those with j = col + n1 n2 < n, contiguous in G) densely into the
+    // staging area behind the column buffer with one bulk copy, counted in
+    // bytes on an mbarrier, as soon as every thread has read the current
+    // column's; the copy runs under the whole transform.  Copy u completes
+    // phase u.
+    static_assert(CA == 1 && B::NBUF == 1 && sizeof(T) == 4, "separate staging: one FP32 column per CTA");
+    static_assert(L * sizeof(PM) < (1u << 20), "mbarrier transaction count");
+    const int n_tiles = n1;
+    const int m_max = (n + n1 - 1) / n1;  // samples in column 0, the most of any column
+    PM* stg = smem + S::LP;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(stg + m_max);
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    unsigned issued = 0, waited = 0;
+    auto issue = [&](int col) {
+      const int m = col < n ? (n - col + n1 - 1) / n1 : 0;
+      fence_proxy_async();  // the staging area's earlier reads precede the copy
+      mbar_expect_tx(bar, (unsigned)(m * sizeof(PM)));
+      if (m > 0) bulk_load(stg, G + (int64_t)col * lc, (unsigned)(m * sizeof(PM)), bar);
+      ++issued;
+    };
+    int tile = blockIdx.x;
+    if (threadIdx.x == 0 && tile < n_tiles) issue(tile);
+    bool all_ok = true;
+    for (; tile < n_tiles; tile += gridDim.x) {
+      // the plan may shorten this wait (tests of the timeout path); the
+      // drain below always keeps the full limit
+      const bool ok = mbar_wait(bar, waited & 1u, wait_limit >= 0 ? wait_limit : kWaitLimit);
+      if (ok) ++waited;
+      all_ok = __syncthreads_and(ok) != 0;
+      if (!all_ok) break;
+      const int next = tile + gridDim.x;
+      pass_a_tile<T, L, CA, V, true>(tile, smem, c, t, G, lc, n, n1, twL, tc, inv_n, Z, NoOp(), stg, [&] {
+        if (threadIdx.x == 0 && next < n_tiles) issue(next);
+      });
+    }
+    if (!all_ok) {
+      // a wait ran out: record it, then give the copy still in flight a
+      // bounded chance to land before the CTA's shared memory goes away
+      if (threadIdx.x == 0) {
+        if (err) atomicCAS(err, 0, FSTAT_ERR_TIMEOUT);
+        for (unsigned u = waited; u < issued; ++u) mbar_wait(bar, u & 1u);
+      }
+      return;
+    }
   } else {
     const int n_tiles = n1 / CA;
     auto stage = [&](int it) { return smem + (B::NBUF == 2 ? (it & 1) : 0) * (CA * S::LP) + c * S::LP; };
@@ -973,24 +1033,33 @@ inline int persistent_grid(int tiles, int ctas, int per_sm, int res) {
   return (!kPipeline || tiles < g) ? tiles : g;
 }
 
+// Dynamic shared memory a CTA may opt into (227 KB on sm_100 / sm_103).
+constexpr size_t kSmemOptIn = (size_t)227 * 1024;
+
 template <typename T, int L, int CA, int V>
-cudaError_t run_a(const void* G, int64_t lc, int64_t n, int n1, const void* twA, const void* hi,
-                  const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st, int res) {
+cudaError_t run_a(const void* G, int64_t lc, int64_t n, int n1, const void* twA, const TmplCoef* coef, void* Z,
+                  int* err, int wait_limit, cudaStream_t st, int res) {
   using S = Shape<T, L, V>;
-  constexpr size_t smem = Buf<T, L, CA, V>::BYTES;
+  using PM = typename S::PM;
+  // separate staging (bit 4): the column buffer, the most samples of any
+  // column (dense) and the mbarrier, sized per launch
+  size_t smem = Buf<T, L, CA, V>::BYTES;
+  if constexpr ((V & 16) != 0) {
+    smem += (size_t)((n + n1 - 1) / n1) * sizeof(PM) + 16;
+    if (smem > kSmemOptIn) return cudaErrorInvalidConfiguration;
+  }
   constexpr int threads = CA * S::TPC;
   static int ctas = 0, per_sm = 0;
   if (!ctas) {
-    cudaError_t e = resident_ctas(k_pass_a<T, L, CA, V>, threads, smem, &ctas, &per_sm);
+    cudaError_t e = resident_ctas(k_pass_a<T, L, CA, V>, threads, (V & 16) ? kSmemOptIn : smem, &ctas, &per_sm);
     if (e != cudaSuccess) return e;
   }
   if (n1 % CA) return cudaErrorInvalidConfiguration;
   const int tiles = n1 / CA;
   using TW = typename S::TW;
   const int grid = persistent_grid(tiles, ctas, per_sm, res);
-  k_pass_a<T, L, CA, V><<<grid, threads, smem, st>>>(
-      (const typename S::PM*)G, lc, (int)n, n1, (const TW*)twA, coef, (typename S::PM*)Z);
-  (void)hi; (void)lo; (void)h;
+  k_pass_a<T, L, CA, V><<<grid, threads, smem, st>>>((const PM*)G, lc, (int)n, n1, (const TW*)twA, coef, (PM*)Z, err,
+                                                     wait_limit);
   return cudaGetLastError();
 }
 
@@ -1068,30 +1137,33 @@ template <int L> constexpr bool wide_variants() { return L >= 512; }
 
 // shape code: c = columns (A) / rows (B) per CTA, 0 = default; v = schedule
 template <typename T, int L, int V>
-cudaError_t pick_a_v(int ca, const void* G, int64_t lc, int64_t n, int n1, const void* twA, const void* hi,
-                     const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st, int res) {
+cudaError_t pick_a_v(int ca, const void* G, int64_t lc, int64_t n, int n1, const void* twA, const TmplCoef* coef,
+                     void* Z, int* err, int wait_limit, cudaStream_t st, int res) {
   switch (ca) {
-    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_a<T, L, 1, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res); break;
-    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_a<T, L, 2, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res); break;
-    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_a<T, L, 4, V>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res); break;
+    case 1: if constexpr (cfg_ok<T, L, 1, V>()) return run_a<T, L, 1, V>(G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res); break;
+    case 2: if constexpr (cfg_ok<T, L, 2, V>()) return run_a<T, L, 2, V>(G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res); break;
+    case 4: if constexpr (cfg_ok<T, L, 4, V>()) return run_a<T, L, 4, V>(G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res); break;
     default: break;
   }
   return cudaErrorInvalidConfiguration;
 }
 
 template <typename T, int L>
-cudaError_t pick_a(int ca, int v, const void* G, int64_t lc, int64_t n, int n1, const void* twA, const void* hi,
-                   const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st, int res) {
+cudaError_t pick_a(int ca, int v, const void* G, int64_t lc, int64_t n, int n1, const void* twA, const TmplCoef* coef,
+                   void* Z, int* err, int wait_limit, cudaStream_t st, int res) {
   using S = Shape<T, L, 0>;
   if (ca <= 0) ca = S::CA_DEF;
-  if (v == 0 && ca == S::CA_DEF) return run_a<T, L, S::CA_DEF, 0>(G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
+  if (v == 0 && ca == S::CA_DEF) return run_a<T, L, S::CA_DEF, 0>(G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res);
   if constexpr (sizeof(T) == 4 && wide_variants<L>()) {
-    if (v == 0) return pick_a_v<T, L, 0>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
-    if (v == 2) return pick_a_v<T, L, 2>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
+    if (v == 0) return pick_a_v<T, L, 0>(ca, G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res);
+    if (v == 2) return pick_a_v<T, L, 2>(ca, G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res);
     if constexpr (L >= 1024) {
-      if (v == 1) return pick_a_v<T, L, 1>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
-      if (v == 3) return pick_a_v<T, L, 3>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
-      if (v == 10) return pick_a_v<T, L, 10>(ca, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
+      if (v == 1) return pick_a_v<T, L, 1>(ca, G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res);
+      if (v == 3) return pick_a_v<T, L, 3>(ca, G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res);
+      if (v == 10) return pick_a_v<T, L, 10>(ca, G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res);
+    }
+    if constexpr (L == 8192 && kPipeline) {
+      if (v == 16 && ca == 1) return run_a<T, L, 1, 16>(G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res);
     }
   }
   return cudaErrorInvalidConfiguration;
@@ -1146,17 +1218,15 @@ cudaError_t pick_b(int cb, int v, const void* Z, int n2, const void* twB, const 
 // 8192-point columns (FP32 only: one padded column of FP64 pairs would not
 // fit shared memory), compiled in a translation unit of their own
 cudaError_t pick_a_8192(int ca, int v, const void* G, int64_t lc, int64_t n, int n1, const void* twA,
-                        const void* hi, const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st,
-                        int res);
+                        const TmplCoef* coef, void* Z, int* err, int wait_limit, cudaStream_t st, int res);
 
 template <typename T>
 cudaError_t dispatch_a(int log2_n2, int ca, int v, const void* G, int64_t lc, int64_t n, int n1, const void* twA,
-                       const void* hi, const void* lo, int h, const TmplCoef* coef, void* Z, cudaStream_t st,
-                       int res = 0) {
+                       const TmplCoef* coef, void* Z, int* err, int wait_limit, cudaStream_t st, int res = 0) {
   switch (log2_n2) {
-    FSTAT_LEN_CASES(pick_a, >(ca, v, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res))
+    FSTAT_LEN_CASES(pick_a, >(ca, v, G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res))
     case 13:
-      if constexpr (sizeof(T) == 4) return pick_a_8192(ca, v, G, lc, n, n1, twA, hi, lo, h, coef, Z, st, res);
+      if constexpr (sizeof(T) == 4) return pick_a_8192(ca, v, G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }

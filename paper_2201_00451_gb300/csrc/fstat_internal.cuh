@@ -198,9 +198,6 @@ cudaError_t launch_grad(const Geo& g, const void* tables, const fstat_candidate*
 struct TwiddleTables {
   const void* a;   // pass A Stockham roots, N2 entries
   const void* b;   // pass B Stockham roots, N1 entries
-  const void* lo;  // W_N^i, i < 2^h
-  const void* hi;  // W_N^(i 2^h)
-  int h;
   size_t bytes;
 };
 TwiddleTables twiddle_layout(int precision, int log2n1, int log2n2, void* base);
@@ -234,12 +231,16 @@ __device__ __forceinline__ unsigned long long band_key(float v, unsigned bin) {
 }
 
 // FFT passes; ca / cb = columns / rows per CTA (0 = default for the length),
-// va / vb = radix schedule (0 = radix-16 first, 1 = radix-8 first).
-// va / vb: bit 0 radix-8 first, bit 1 single shared buffer.  res > 0:
-// persistent grid of at most res CTAs per SM (0 = every resident CTA).
+// va / vb = radix schedule: bit 0 radix-8 first, bit 1 single shared
+// buffer, bit 2 (pass B) tiles by bulk tensor copies, bit 3 (pass A) three
+// CTAs per SM, va 16 (8192-point columns) the next column's samples staged
+// by a bulk copy under the transform.  res > 0: persistent grid of at most
+// res CTAs per SM (0 = every resident CTA).  err: where a pass records a
+// timed-out wait (FSTAT_ERR_TIMEOUT), or nullptr; wait_limit >= 0: polls of
+// pass A's staged-column waits (timeout tests).
 cudaError_t launch_pass_a_f32(int log2_n2, int ca, int va, const void* G, int64_t lc, int64_t n, int n1,
-                              const void* twA, const void* hi, const void* lo, int h, const TmplCoef* coef,
-                              void* Z, cudaStream_t st, int res = 0);
+                              const void* twA, const TmplCoef* coef, void* Z, cudaStream_t st, int res = 0,
+                              int* err = nullptr, int wait_limit = -1);
 // pk == nullptr: write 2F to out[n_fft]; otherwise reduce it as pk says.
 // err: where a pass records a timed-out wait (FSTAT_ERR_TIMEOUT), or nullptr
 // wait_limit >= 0: polls of each tile's first bulk-copy wait (timeout tests)
@@ -248,8 +249,8 @@ cudaError_t launch_pass_b_f32(int log2_n1, int cb, int vb, const void* Z, int n2
                               const PeakArgs* pk = nullptr, int res = 0, int* err = nullptr,
                               int wait_limit = -1);
 cudaError_t launch_pass_a_f64(int log2_n2, int ca, int va, const void* G, int64_t lc, int64_t n, int n1,
-                              const void* twA, const void* hi, const void* lo, int h, const TmplCoef* coef,
-                              void* Z, cudaStream_t st, int res = 0);
+                              const void* twA, const TmplCoef* coef, void* Z, cudaStream_t st, int res = 0,
+                              int* err = nullptr, int wait_limit = -1);
 cudaError_t launch_pass_b_f64(int log2_n1, int cb, int vb, const void* Z, int n2, const void* twB,
                               const SkyConst* sky, float* out, cudaStream_t st,
                               const PeakArgs* pk = nullptr, int res = 0, int* err = nullptr,

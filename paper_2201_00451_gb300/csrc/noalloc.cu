@@ -139,7 +139,7 @@ extern "C" int fstat_twoF_noalloc(const void* g_pairs, int64_t n_samples, int64_
   cudaError_t e = build_twiddles(FSTAT_MIXED, log2n1, log2n2, p.tw, st);
   if (e != cudaSuccess) return FSTAT_ERR_CUDA;
   TwiddleTables tt = twiddle_layout(FSTAT_MIXED, log2n1, log2n2, p.tw);
-  e = launch_pass_a_f32(log2n2, 0, 0, p.G, lc, n_samples, n1, tt.a, tt.hi, tt.lo, tt.h, p.coef, p.Z, st);
+  e = launch_pass_a_f32(log2n2, 0, 0, p.G, lc, n_samples, n1, tt.a, p.coef, p.Z, st);
   if (e != cudaSuccess) return FSTAT_ERR_CUDA;
   e = launch_pass_b_f32(log2n1, 0, 0, p.Z, n2, tt.b, p.sky, twoF, st);
   if (e != cudaSuccess) return FSTAT_ERR_CUDA;

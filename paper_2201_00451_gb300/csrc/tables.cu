@@ -1,11 +1,10 @@
 // Twiddle tables for the FFT passes: roots of unity exp(-2 pi i m / M),
 // evaluated in FP64 (sincospi) and stored in the path's precision.
 //
-// Layout of one table block for n_fft = N1 * N2 = 2^(l1 + l2), h = ceil((l1 + l2) / 2):
+// Layout of one table block for n_fft = N1 * N2 = 2^(l1 + l2):
 //   [ tw_A : N2 entries, M = N2 ]   Stockham twiddles of pass A
 //   [ tw_B : N1 entries, M = N1 ]   Stockham twiddles of pass B
-//   [ lo   : 2^h entries, M = N ]   W_N^i,         i < 2^h
-//   [ hi   : N/2^h entries, M = N/2^h ]  W_N^{i 2^h}
+// (the four-step twiddles W_N^{n1 k2} are computed in pass A itself)
 #include "fstat_internal.cuh"
 
 namespace fstat {
@@ -46,31 +45,22 @@ int device_sm_count() {
 
 TwiddleTables twiddle_layout(int precision, int log2n1, int log2n2, void* base) {
   TwiddleTables t{};
-  const int log2n = log2n1 + log2n2;
-  t.h = (log2n + 1) / 2;
   const size_t eb = precision == FSTAT_FP64 ? 16 : 8;
   char* p = (char*)base;
   t.a = p; p += eb * ((size_t)1 << log2n2);
   t.b = p; p += eb * ((size_t)1 << log2n1);
-  t.lo = p; p += eb * ((size_t)1 << t.h);
-  t.hi = p; p += eb * ((size_t)1 << (log2n - t.h));
   t.bytes = (size_t)(p - (char*)base);
   return t;
 }
 
 cudaError_t build_twiddles(int precision, int log2n1, int log2n2, void* base, cudaStream_t st) {
   TwiddleTables t = twiddle_layout(precision, log2n1, log2n2, base);
-  const int log2n = log2n1 + log2n2;
   if (precision == FSTAT_FP64) {
     roots((double2*)t.a, log2n2, st);
     roots((double2*)t.b, log2n1, st);
-    k_roots<double2><<<((1 << t.h) + 255) / 256, 256, 0, st>>>((double2*)t.lo, 1 << t.h, log2n);
-    roots((double2*)t.hi, log2n - t.h, st);
   } else {
     roots((float2*)t.a, log2n2, st);
     roots((float2*)t.b, log2n1, st);
-    k_roots<float2><<<((1 << t.h) + 255) / 256, 256, 0, st>>>((float2*)t.lo, 1 << t.h, log2n);
-    roots((float2*)t.hi, log2n - t.h, st);
   }
   return cudaGetLastError();
 }

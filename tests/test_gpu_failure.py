@@ -67,6 +67,30 @@ def test_wait_that_runs_out_reports_timeout_and_the_plan_recovers(vb):
     assert _ok(out, ref)
 
 
+def test_staged_column_wait_that_runs_out_reports_timeout_and_the_plan_recovers():
+    # pass A's schedule 16 (8192-point columns whose samples arrive by one
+    # bulk copy each): every CTA's first wait gives up at once, the copy in
+    # flight is drained under the full limit, the kernel returns
+    t = _target()
+    x = synth.make_data(t)
+    tm = t.templates()
+    ref = resamp.fstat(t, x, tm)
+    with pkg.FstatPlan.from_target(t) as plan:
+        for X in range(2):
+            plan.set_data(X, x[X], t.sigmas[X])
+        plan.set_split(128)            # pass A 8192 points
+        plan.set_cta(1, 0, 16, 0)
+        plan.set_wait_limit(0)
+        plan.compute(tm)
+        with pytest.raises(pkg.FstatError) as e:
+            plan.sync()
+        assert e.value.code == TIMEOUT
+        plan.set_wait_limit(-1)
+        out = plan.compute(tm).cpu().numpy()
+        plan.sync()
+    assert _ok(out, ref)
+
+
 def test_device_memory_cap_gives_oom_and_leaves_plans_usable(monkeypatch):
     t = _target()
     x = synth.make_data(t)

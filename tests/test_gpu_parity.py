@@ -255,6 +255,51 @@ def test_register_caps_and_tma_loads_give_identical_2F():
     assert_parity(base, resamp.fstat(t, x, tm))
 
 
+@pytest.mark.parametrize("n", [600_001, 1_000_003, 1_400_001])
+def test_staged_8192_point_columns_give_identical_2F(n):
+    # Pass A's schedule 16 stages the next column's samples densely in shared
+    # memory of their own (one bulk copy) instead of at padded positions in
+    # the column buffer: the same arithmetic, bitwise equal 2F.  600 001
+    # samples leave the upper half of every column empty (the half-size
+    # first butterflies); 1 400 001 is the most samples per column
+    # (5469 of 8192) whose staging still fits beside the column buffer.
+    t = small(seed=17, n_fft=1 << 21, n_samples=n, dt=1.0)
+    x = synth.make_data(t)
+    tm = t.templates()[:3]
+    with pkg.FstatPlan.from_target(t) as plan:
+        for X in range(2):
+            plan.set_data(X, x[X], t.sigmas[X])
+        plan.set_split(256)            # pass A 8192 points, pass B 256
+        plan.set_cta(1, 0, 0, 0)
+        base = plan.compute(tm).cpu().numpy()
+        plan.set_cta(1, 0, 16, 0)
+        assert plan.cta[1] == 16
+        assert np.array_equal(plan.compute(tm).cpu().numpy(), base)
+        plan.sync()
+    assert_parity(base, resamp.fstat(t, x, tm))
+
+
+def test_staged_8192_point_columns_refused_when_the_staging_does_not_fit():
+    # 2 000 003 samples over 256 columns: 7813 per column, whose staging
+    # (122 KB) does not fit beside the 136 KB column buffer; the launch is
+    # refused before anything runs and the plan stays usable.
+    t = small(seed=19, n_fft=1 << 21, n_samples=2_000_003, dt=1.0)
+    x = synth.make_data(t)
+    tm = t.templates()[:2]
+    with pkg.FstatPlan.from_target(t) as plan:
+        for X in range(2):
+            plan.set_data(X, x[X], t.sigmas[X])
+        plan.set_split(256)
+        plan.set_cta(1, 0, 16, 0)
+        with pytest.raises(pkg.FstatError) as e:
+            plan.compute(tm)
+        assert e.value.code == -3
+        plan.set_cta(1, 0, 0, 0)
+        out = plan.compute(tm).cpu().numpy()
+        plan.sync()
+    assert_parity(out, resamp.fstat(t, x, tm))
+
+
 @pytest.mark.parametrize("t_ref_days", [-40.0, -450.0, 500.0])
 def test_reference_time_far_outside_the_data(t_ref_days):
     # A spindown reference time far from the data (up to ~2.2e7 samples of
