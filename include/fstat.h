@@ -300,12 +300,17 @@ int fstat_set_split(fstat_plan* plan, int64_t n1);
  * only: bit 2 = pass B tile loads by the tensor-memory-access engine
  * (FP32, rows of 1024 points or more; a load that does not complete within
  * a bounded wait ends the kernel, and fstat_sync() then returns
- * FSTAT_ERR_TIMEOUT); va 16 (FP32, 8192-point columns, one per CTA) =
- * the next column's samples copied by one bulk copy into shared memory of
+ * FSTAT_ERR_TIMEOUT); va 16 (FP32, 8192-point columns, one per CTA) and
+ * va 18 (FP32, 4096-point columns, one per CTA, two CTAs per SM) = the
+ * next column's samples copied by one bulk copy into shared memory of
  * their own while the current column is transformed (the plan's samples
  * per column must fit beside the column buffer; a copy that does not
  * complete within a bounded wait likewise gives FSTAT_ERR_TIMEOUT).  va
- * 0..3, 10 or 16, vb 0..7.  A shape that is not
+ * 0..3, 10, 16 or 18.  vb 8 (FP32 rows of 1024 points or more, not
+ * with fstat_compute_peaks) = the first half of the next tile's rows copied
+ * into shared memory of their own as soon as the current tile's first pass
+ * has read its own, the second half once its last pass has read the
+ * buffer.  vb 0..8.  A shape that is not
  * compiled for the current split makes fstat_compute return
  * FSTAT_ERR_CUDA.  fstat_get_cta reports the shapes in effect (a default
  * as its value for the current split). */

@@ -463,10 +463,11 @@ class FstatPlan:
 
     def set_cta(self, ca: int, cb: int, va: int = 0, vb: int = 0):
         """fstat_set_cta: columns per CTA of pass A (ca), rows per CTA of pass
-        B (cb), 0 = the length's default; schedules va (0..3, 10 or 16) and vb
-        (0..7): bit 0 radix-8 first, bit 1 one buffer (register-capped for
-        two CTAs per SM), bit 2 pass-B tiles by TMA, bit 3 pass A three CTAs
-        per SM."""
+        B (cb), 0 = the length's default; schedules va (0..3, 10, 16 or 18)
+        and vb (0..8): bit 0 radix-8 first, bit 1 one buffer
+        (register-capped for two CTAs per SM), bit 2 pass-B tiles by TMA,
+        bit 3 pass A three CTAs per SM, va 16 / 18 columns staged apart, vb
+        8 half of the next pass-B tile staged apart."""
         _check(self._lib.fstat_set_cta(self._p, int(ca), int(va), int(cb), int(vb)), "fstat_set_cta")
 
     def set_streams(self, n: int):

@@ -62,10 +62,15 @@ template <> struct TwT<double> { using type = double2; };
 // 256 threads a register cap (128) that lets two CTAs share an SM; bit 3
 // (pass A, with bit 1, radix-16) = a tighter cap (80) for three CTAs per
 // SM; bit 2 (pass B) = tiles loaded by bulk tensor copies (TMA) instead of
-// per-thread 16-byte copies; bit 2 (pass A, fused kernel only) = the
-// column staged densely by one bulk copy; bit 4 (pass A, 8192-point
-// columns) = the next column's samples copied densely by one bulk copy into
-// a staging area of their own while this column is transformed.  The first
+// per-thread 16-byte copies; bit 3 (pass B, per-thread copies, one
+// buffer) = the first half of the next tile's rows copied into a staging
+// area of their own as soon as the first pass has read this tile's (the
+// second half as before, once the last pass has read the buffer); bit 2
+// (pass A, fused kernel only) = the
+// column staged densely by one bulk copy; bit 4 (pass A, one column per
+// CTA: 16 at 8192 points, 18 at 4096 points with the two-per-SM register
+// cap of bit 1) = the next column's samples copied densely by one bulk copy
+// into a staging area of their own while this column is transformed.  The first
 // radix is the largest.
 __host__ __device__ constexpr bool r8(int L, int V) { return (V & 1) && L >= 1024; }
 __host__ __device__ constexpr int np_of(int L, int V) {
@@ -119,7 +124,7 @@ template <typename T, int L, int V = 0> struct Shape {
 constexpr size_t kSmemCap = (size_t)220 * 1024;
 template <typename T, int L, int C, int V = 0> struct Buf {
   static constexpr size_t ONE = (size_t)C * Shape<T, L, V>::LP * sizeof(typename Shape<T, L, V>::PM);
-  static constexpr int NBUF = (kPipeline && !(V & 2) && !(V & 16) && 2 * ONE <= kSmemCap) ? 2 : 1;
+  static constexpr int NBUF = (kPipeline && !(V & 2) && !(V & 8) && !(V & 16) && 2 * ONE <= kSmemCap) ? 2 : 1;
   static constexpr size_t BYTES = NBUF * ONE;
 };
 
@@ -769,12 +774,16 @@ __device__ __forceinline__ void peak_epilogue(const float* sf, int k2_0, int n2,
   }
 }
 
-template <typename T, int L, int CB, int V, bool STAGED, int MODE, typename F = NoOp>
+// Schedule bit 3: rows [0, L/2) of the tile come from `stg` (same layout
+// as the buffer), and at_staged() runs once every thread has read them.
+template <typename T, int L, int CB, int V, bool STAGED, int MODE, typename F = NoOp, typename H = NoOp>
 __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type* buf, int c, int t,
                                             const typename PairMem<T>::type* __restrict__ Z, int n2,
                                             const typename TwT<T>::type* __restrict__ twL, T kA, T kB, T kC,
                                             float* __restrict__ out, const PeakArgs& pk,
-                                            unsigned long long* ks, float* sf_sep, const F& at_free = F()) {
+                                            unsigned long long* ks, float* sf_sep, const F& at_free = F(),
+                                            const typename PairMem<T>::type* stg = nullptr,
+                                            const H& at_staged = H()) {
   using S = Shape<T, L, V>;
   const int k2 = tile * CB + c;
   constexpr int NB = S::R0 / S::RL;
@@ -796,9 +805,13 @@ __device__ __forceinline__ void pass_b_tile(int tile, typename PairMem<T>::type*
   constexpr bool kDense = (V & 4) != 0;
 #pragma unroll
   for (int s = 0; s < S::R0; ++s)
-    v[s] = STAGED ? pload(buf + (kDense ? t + s * S::TPC : pad_idx(t + s * S::TPC, S::PS)) * CB)
+    v[s] = STAGED ? pload(((V & 8) && s < S::R0 / 2 ? stg : buf) +
+                          (kDense ? t + s * S::TPC : pad_idx(t + s * S::TPC, S::PS)) * CB)
                   : pload_g(Z + (int64_t)(t + s * S::TPC) * n2 + k2);
-  if constexpr (STAGED) __syncthreads();  // the staged rows are overwritten below
+  if constexpr (STAGED) {
+    __syncthreads();  // the staged rows are overwritten below
+    at_staged();
+  }
   dft<T, S::R0>(v);
   store_pass0<T, L, V, CB>(v, buf, t);
   passes<T, L, V, CB, 1, kPassBTable && sizeof(T) == 4, F>(v, buf, t, twL, at_free);
@@ -953,20 +966,31 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
   } else {
     const int n_tiles = n2 / CB;
     auto stage = [&](int it) { return smem + (B::NBUF == 2 ? (it & 1) : 0) * (CB * S::LP) + c; };
-    auto prefetch = [&](int tile, PM* dst) {
+    // rows [s0 R0/16 .. ) of the tile: s in [s0, s1) of each thread's rows t + s TPC
+    auto prefetch_rows = [&](int tile, PM* dst, int s0, int s1) {
       const int k2 = tile * CB + c;
 #pragma unroll
       for (int s = 0; s < S::R0; ++s) {
+        if (s < s0 || s >= s1) continue;
         const int n1 = t + s * S::TPC;
         cp_pair(dst + pad_idx(n1, S::PS) * CB, Z + (int64_t)n1 * n2 + k2);
       }
     };
+    // bit 3: the first half of the rows in their own staging area
+    constexpr bool kSplit = (V & 8) != 0;
+    static_assert(!kSplit || (B::NBUF == 1 && MODE != kPeaks && sizeof(T) == 4), "split staging: one buffer");
+    PM* stg = kSplit ? smem + CB * S::LP + c : nullptr;
+    constexpr int kLo = kSplit ? S::R0 / 2 : 0;
+    auto prefetch = [&](int tile, PM* dst) { prefetch_rows(tile, dst, kLo, S::R0); };
     // with one buffer (and no peaks epilogue that reuses it) the next
     // tile's copies start as soon as the last Stockham pass has read it
     constexpr bool kEarly = B::NBUF == 1 && (MODE != kPeaks || PeakSmem<T, L, CB, V>::SEP);
     int tile = blockIdx.x;
     if constexpr (B::NBUF == 2 || kEarly) {
-      if (tile < n_tiles) prefetch(tile, stage(0));
+      if (tile < n_tiles) {
+        if constexpr (kSplit) prefetch_rows(tile, stg, 0, kLo);
+        prefetch(tile, stage(0));
+      }
       cp_async_commit();
     }
     for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
@@ -987,10 +1011,18 @@ k_pass_b(const typename PairMem<T>::type* __restrict__ Z, int n2,
       if constexpr (kEarly) {
         // no barrier after the tile: it stopped reading the buffer before
         // the barrier at which the next tile's copies were issued
-        pass_b_tile<T, L, CB, V, true, MODE>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks, sf_sep, [&] {
-          if (next < n_tiles) prefetch(next, buf);
-          cp_async_commit();
-        });
+        pass_b_tile<T, L, CB, V, true, MODE>(
+            tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks, sf_sep,
+            [&] {
+              if (next < n_tiles) prefetch(next, buf);
+              cp_async_commit();
+            },
+            stg, [&] {
+              if constexpr (kSplit) {
+                if (next < n_tiles) prefetch_rows(next, stg, 0, kLo);
+                cp_async_commit();
+              }
+            });
       } else {
         pass_b_tile<T, L, CB, V, true, MODE>(tile, buf, c, t, Z, n2, twL, kA, kB, kC, out, pk, ks, sf_sep);
         __syncthreads();  // this buffer is the prefetch target two tiles on
@@ -1049,10 +1081,14 @@ cudaError_t run_a(const void* G, int64_t lc, int64_t n, int n1, const void* twA,
     if (smem > kSmemOptIn) return cudaErrorInvalidConfiguration;
   }
   constexpr int threads = CA * S::TPC;
+  // resident CTAs for this launch's shared memory (separate staging: it
+  // depends on the plan, so the query is redone when it changes)
   static int ctas = 0, per_sm = 0;
-  if (!ctas) {
-    cudaError_t e = resident_ctas(k_pass_a<T, L, CA, V>, threads, (V & 16) ? kSmemOptIn : smem, &ctas, &per_sm);
+  static size_t ctas_smem = 0;
+  if (!ctas || ctas_smem != smem) {
+    cudaError_t e = resident_ctas(k_pass_a<T, L, CA, V>, threads, smem, &ctas, &per_sm);
     if (e != cudaSuccess) return e;
+    ctas_smem = smem;
   }
   if (n1 % CA) return cudaErrorInvalidConfiguration;
   const int tiles = n1 / CA;
@@ -1105,7 +1141,11 @@ template <typename T, int L, int CB, int V, int MODE>
 cudaError_t run_b(const void* Z, int n2, const void* twB, const SkyConst* sky, float* out, const PeakArgs& pk,
                   cudaStream_t st, int res) {
   using S = Shape<T, L, V>;
-  constexpr size_t smem = MODE == kPeaks ? PeakSmem<T, L, CB, V>::BYTES : Buf<T, L, CB, V>::BYTES;
+  // split staging (bit 3): half a tile more
+  constexpr size_t smem = MODE == kPeaks ? PeakSmem<T, L, CB, V>::BYTES
+                          : (V & 8)      ? Buf<T, L, CB, V>::BYTES + Buf<T, L, CB, V>::ONE / 2
+                                         : Buf<T, L, CB, V>::BYTES;
+  if constexpr (smem > kSmemOptIn) return cudaErrorInvalidConfiguration;
   constexpr int threads = CB * S::TPC;
   static_assert(MODE != kPeaks || (L * CB * sizeof(float) <= Buf<T, L, CB, V>::ONE), "peaks epilogue reuses the stage");
   static_assert(MODE != kPeaks || threads % 32 == 0, "peaks epilogue works on whole warps");
@@ -1165,6 +1205,9 @@ cudaError_t pick_a(int ca, int v, const void* G, int64_t lc, int64_t n, int n1, 
     if constexpr (L == 8192 && kPipeline) {
       if (v == 16 && ca == 1) return run_a<T, L, 1, 16>(G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res);
     }
+    if constexpr (L == 4096 && kPipeline) {  // 256 threads: two CTAs per SM
+      if (v == 18 && ca == 1) return run_a<T, L, 1, 18>(G, lc, n, n1, twA, coef, Z, err, wait_limit, st, res);
+    }
   }
   return cudaErrorInvalidConfiguration;
 }
@@ -1199,6 +1242,9 @@ cudaError_t pick_b(int cb, int v, const void* Z, int n2, const void* twB, const 
         if (v == 5) return pick_b_v<T, L, 5, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
         if (v == 6) return pick_b_v<T, L, 6, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
         if (v == 7) return pick_b_v<T, L, 7, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
+        if constexpr (MODE != kPeaks) {  // half the next tile staged apart
+          if (v == 8) return pick_b_v<T, L, 8, MODE>(cb, Z, n2, twB, sky, out, pk, st, res);
+        }
       }
     }
   }

@@ -1123,8 +1123,8 @@ int fstat_set_wait_limit(fstat_plan* p, int polls) {
 }
 
 int fstat_set_cta(fstat_plan* p, int ca, int va, int cb, int vb) {
-  if (!p || ca < 0 || cb < 0 || ca > 32 || cb > 32 || va < 0 || (va > 3 && va != 10 && va != 16) || vb < 0 ||
-      vb > 7)
+  if (!p || ca < 0 || cb < 0 || ca > 32 || cb > 32 || va < 0 || (va > 3 && va != 10 && va != 16 && va != 18) || vb < 0 ||
+      vb > 8)
     return FSTAT_ERR_INVALID_ARG;
   p->ca = ca;
   p->va = va;
@@ -1149,7 +1149,7 @@ std::string tune_key(const fstat_plan* p) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) prop.name[0] = 0;
   char buf[400];
-  std::snprintf(buf, sizeof buf, "v3|%s|N=%lld|nfft=%lld|prec=%d|ndet=%d|ns=%d", prop.name,
+  std::snprintf(buf, sizeof buf, "v4|%s|N=%lld|nfft=%lld|prec=%d|ndet=%d|ns=%d", prop.name,
                 (long long)p->d.n_samples, (long long)p->d.n_fft, p->d.precision, p->d.n_det, p->nstream);
   for (char* c = buf; *c; ++c)
     if (*c == ' ' || *c == '\t') *c = '_';
@@ -1257,15 +1257,16 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
     std::vector<std::pair<float, std::pair<int, int>>> ta, tb;
     // schedules: radix-8 first (bit 0), one buffer (bit 1), for pass B tile
     // loads by the tensor-memory-access engine (bit 2), for pass A three
-    // CTAs per SM (bit 3) and 8192-point columns staged apart (16)
-    static const int kVa[] = {0, 1, 2, 3, 10, 16};
+    // CTAs per SM (bit 3) and columns staged apart (16 at 8192 points, 18 at
+    // 4096), for pass B half of the next tile staged apart (8)
+    static const int kVa[] = {0, 1, 2, 3, 10, 16, 18};
     for (int v : kVa) {
       for (int c : kCa) {
         float ms = time_pass(p, 0, c, v, p->d_coef, out, st, e0, e1);
         if (ms > 0.f) ta.push_back({ms, {c, v}});
       }
     }
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v <= 8; ++v) {
       for (int c : kCb) {
         float ms = time_pass(p, 1, c, v, p->d_coef, out, st, e0, e1);
         if (ms > 0.f) tb.push_back({ms, {c, v}});

@@ -53,10 +53,11 @@ def test_every_split_and_cta_shape(log2n, n):
             plan.set_split(1 << l1)
             # radix-8 first (bit 0), one shared buffer (bit 1), pass B tile
             # loads by TMA (bit 2, rows of 1024 points or more), pass A
-            # three CTAs per SM (va 10) and 8192-point columns staged apart
-            # (va 16, one column per CTA)
-            for v in range(10):
-                va, vb = {8: (10, 2), 9: (16, 0)}.get(v, (v & 3, v))
+            # three CTAs per SM (va 10), and columns staged apart (va 16 at
+            # 8192 points, 18 at 4096; one column per CTA)
+            # and pass B with half of the next tile staged apart (vb 8)
+            for v in range(12):
+                va, vb = {8: (10, 2), 9: (16, 0), 10: (18, 6), 11: (2, 8)}.get(v, (v & 3, v))
                 for ca, cb in [(0, 0), (1, 1), (2, 2), (4, 4), (1, 8), (2, 8)]:
                     plan.set_cta(ca, cb, va, vb)
                     # the two templates swap places from one shape to the

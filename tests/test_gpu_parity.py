@@ -245,13 +245,36 @@ def test_register_caps_and_tma_loads_give_identical_2F():
         plan.set_split(1024)           # pass A 1024 points, pass B 1024 points
         plan.set_cta(1, 4, 0, 0)
         base = plan.compute(tm).cpu().numpy()
-        for ca, cb, va, vb in ((1, 4, 2, 2), (1, 4, 10, 4), (1, 4, 10, 6), (1, 2, 2, 6), (2, 8, 2, 4)):
+        # and pass B with half of each next tile staged apart (vb 8)
+        for ca, cb, va, vb in ((1, 4, 2, 2), (1, 4, 10, 4), (1, 4, 10, 6), (1, 2, 2, 6), (2, 8, 2, 4),
+                               (1, 4, 2, 8), (1, 8, 10, 8), (2, 1, 0, 8)):
             plan.set_cta(ca, cb, va, vb)
             assert plan.cta == (ca, va, cb, vb)
             assert np.array_equal(plan.compute(tm).cpu().numpy(), base), (ca, cb, va, vb)
-        for bad in ((1, 4, 4, 0), (1, 4, 11, 0), (1, 4, 0, 8)):
+        for bad in ((1, 4, 4, 0), (1, 4, 11, 0), (1, 4, 0, 9)):
             with pytest.raises(pkg.FstatError):
                 plan.set_cta(*bad)
+    assert_parity(base, resamp.fstat(t, x, tm))
+
+
+@pytest.mark.parametrize("n", [300_001, 1_000_003])
+def test_staged_4096_point_columns_give_identical_2F(n):
+    # Schedule 18: 4096-point columns (256 threads, two CTAs per SM where
+    # the staging allows) with the next column staged apart, against
+    # schedule 2 (staged in the column buffer): bitwise equal 2F.
+    t = small(seed=23, n_fft=1 << 20, n_samples=n, dt=1.0)
+    x = synth.make_data(t)
+    tm = t.templates()[:3]
+    with pkg.FstatPlan.from_target(t) as plan:
+        for X in range(2):
+            plan.set_data(X, x[X], t.sigmas[X])
+        plan.set_split(256)            # pass A 4096 points, pass B 256
+        plan.set_cta(1, 0, 2, 0)
+        base = plan.compute(tm).cpu().numpy()
+        plan.set_cta(1, 0, 18, 0)
+        assert plan.cta[1] == 18
+        assert np.array_equal(plan.compute(tm).cpu().numpy(), base)
+        plan.sync()
     assert_parity(base, resamp.fstat(t, x, tm))
 
 
