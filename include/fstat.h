@@ -259,6 +259,23 @@ int fstat_semicoherent(fstat_plan* const* seg, int n_seg, const fstat_template* 
 int fstat_grad(fstat_plan* plan, const fstat_candidate* cand, int64_t n, float* twoF, float* grad,
                void* stream);
 
+/* Gradient ascent on 2F (the statistic and gradient of fstat_grad) from n
+ * starting candidates, with the whole loop on the device.  Per step and
+ * candidate, with s = scales (the natural spacings of f, f1dot, alpha,
+ * delta, all > 0) and g = d2F/d(f, f1dot, alpha, delta) at the current
+ * point theta:
+ *   trial = theta + eta (g s) s / |g s|,
+ * evaluated like fstat_grad; if its 2F is larger the trial is taken and
+ * eta grows by 1.25, else theta stays and eta halves (eta starts at
+ * step0 > 0; f2dot is held).  `cand`: HOST array of n starting candidates;
+ * `out`: HOST array receiving the n final candidates (may be `cand`);
+ * `hist`: HOST (steps + 1) x n floats receiving 2F at theta after each
+ * step (row 0: the start), or NULL.  0 <= steps <= 100000.  The ascent state
+ * stays in the plan's device memory between calls.  Synchronises `stream`.
+ * Errors: INVALID_ARG, NOT_READY, OOM, CUDA. */
+int fstat_refine(fstat_plan* plan, const fstat_candidate* cand, int64_t n, const double* scales, int steps,
+                 double step0, fstat_candidate* out, float* hist, void* stream);
+
 /* Frequency axis of the output: f_m = *f0 + m * *df. */
 int fstat_freq_axis(const fstat_plan* plan, double* f0, double* df);
 

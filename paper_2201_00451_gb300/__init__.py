@@ -49,6 +49,7 @@ EXPORTS = (
     "fstat_compute_peaks", "fstat_semicoherent", "fstat_set_residency", "fstat_get_residency",
     "fstat_set_sfts", "fstat_export_data", "fstat_reduce_peaks", "fstat_set_wait_limit",
     "fstat_probe_fma", "fstat_launch_count", "fstat_set_fused", "fstat_get_fused", "fstat_probe_dft16",
+    "fstat_refine",
 )
 
 
@@ -142,6 +143,7 @@ def open_library(path: str) -> ctypes.CDLL:
         "fstat_set_cta": (i32, [P, i32, i32, i32, i32]),
         "fstat_autotune": (i32, [P, P]),
         "fstat_grad": (i32, [P, P, i64, P, P, P]),
+        "fstat_refine": (i32, [P, P, i64, P, i32, dbl, P, P, P]),
         "fstat_batch_create": (i32, [ctypes.POINTER(P)]),
         "fstat_batch_add": (i32, [P, P, P, i64, P, i64]),
         "fstat_batch_instantiate": (i32, [P, P]),
@@ -401,6 +403,23 @@ class FstatPlan:
                                   ctypes.c_void_p(g.data_ptr()), _stream_handle(stream))
         _check(rc, "fstat_grad")
         return two_f, g
+
+    def refine(self, candidates, scales, steps: int = 20, step0: float = 0.25, stream=None):
+        """fstat_refine: gradient ascent on 2F on the device.  Returns (the
+        final candidates as a CANDIDATE_DTYPE array, 2F after each step
+        [steps + 1, n] float32)."""
+        c = np.ascontiguousarray(candidates, dtype=CANDIDATE_DTYPE)
+        n = len(c)
+        sc = np.ascontiguousarray(scales, dtype=np.float64)
+        if sc.shape != (4,):
+            raise ValueError("scales: 4 values (f, f1dot, alpha, delta)")
+        out = np.empty(n, dtype=CANDIDATE_DTYPE)
+        hist = np.empty((int(steps) + 1, n), dtype=np.float32)
+        rc = self._lib.fstat_refine(self._p, ctypes.c_void_p(c.ctypes.data), n, ctypes.c_void_p(sc.ctypes.data),
+                                    int(steps), float(step0), ctypes.c_void_p(out.ctypes.data),
+                                    ctypes.c_void_p(hist.ctypes.data), _stream_handle(stream))
+        _check(rc, "fstat_refine")
+        return out, hist
 
     def freq_axis(self):
         f0, df = ctypes.c_double(), ctypes.c_double()

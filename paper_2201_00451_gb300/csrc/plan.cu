@@ -19,6 +19,7 @@
 #include <string>
 #include <vector>
 
+#include "ascent.cuh"
 #include "fstat_internal.cuh"
 #include "reduce_peaks.cuh"
 #include "sft.cuh"
@@ -95,6 +96,8 @@ struct fstat_plan {
   int64_t ccap = 0;
   void* gscratch = nullptr;
   size_t gscratch_bytes = 0;
+  void* rbuf = nullptr;   // fstat_refine's ascent state and 2F history
+  size_t rbuf_bytes = 0;
   cudaEvent_t cand_staged = nullptr;
   bool cand_pending = false;
   // profiling (kernel kinds 0 = pass A, 1 = pass B, 2 = per-sky work,
@@ -182,6 +185,7 @@ void free_all(fstat_plan* p) {
   if (p->h_cand) cudaFreeHost(p->h_cand);
   if (p->d_cand) cudaFree(p->d_cand);
   if (p->gscratch) cudaFree(p->gscratch);
+  if (p->rbuf) cudaFree(p->rbuf);
   if (p->keys) cudaFree(p->keys);
   if (p->fq) cudaFree(p->fq);
   if (p->cand_staged) cudaEventDestroy(p->cand_staged);
@@ -914,17 +918,17 @@ int fstat_compute_peaks(fstat_plan* p, const fstat_template* tmpl, int64_t n_tmp
   return FSTAT_OK;
 }
 
-int fstat_grad(fstat_plan* p, const fstat_candidate* cand, int64_t n, float* twoF, float* grad,
-               void* stream) {
-  if (!p || n < 0 || (n > 0 && (!cand || !twoF || !grad)) || n > INT32_MAX) return FSTAT_ERR_INVALID_ARG;
-  for (int X = 0; X < p->d.n_det; ++X)
-    if (!p->have[X]) return FSTAT_ERR_NOT_READY;
+static bool candidates_finite(const fstat_candidate* cand, int64_t n) {
   for (int64_t i = 0; i < n; ++i)
     if (!std::isfinite(cand[i].f) || !std::isfinite(cand[i].f1dot) || !std::isfinite(cand[i].alpha) ||
         !std::isfinite(cand[i].delta) || !std::isfinite(cand[i].f2dot))
-      return FSTAT_ERR_INVALID_ARG;
-  if (n == 0) return FSTAT_OK;
-  cudaStream_t st = (cudaStream_t)stream;
+      return false;
+  return true;
+}
+
+// the gradient's sample tables (built once per data set) and scratch for n
+// candidates
+static int grad_prepare(fstat_plan* p, int64_t n, cudaStream_t st) {
   if (!p->gtab) CK(palloc(p, &p->gtab, grad_table_bytes(p->d.n_det, p->d.n_samples)));
   if (!p->gtab_valid) {
     const void* xh[kMaxDet];
@@ -932,6 +936,29 @@ int fstat_grad(fstat_plan* p, const fstat_candidate* cand, int64_t n, float* two
     CK(launch_grad_tables(p->geo, xh, p->dtype, p->gtab, st));
     p->gtab_valid = true;
   }
+  const size_t need = grad_scratch_bytes((int)n, p->geo);
+  if (need > p->gscratch_bytes) {
+    CK(cudaDeviceSynchronize());
+    if (p->gscratch) cudaFree(p->gscratch);
+    p->alloc_bytes -= p->gscratch_bytes;
+    p->gscratch = nullptr;
+    p->gscratch_bytes = 0;
+    CK(palloc(p, &p->gscratch, need));
+    p->gscratch_bytes = need;
+  }
+  return FSTAT_OK;
+}
+
+int fstat_grad(fstat_plan* p, const fstat_candidate* cand, int64_t n, float* twoF, float* grad,
+               void* stream) {
+  if (!p || n < 0 || (n > 0 && (!cand || !twoF || !grad)) || n > INT32_MAX) return FSTAT_ERR_INVALID_ARG;
+  for (int X = 0; X < p->d.n_det; ++X)
+    if (!p->have[X]) return FSTAT_ERR_NOT_READY;
+  if (!candidates_finite(cand, n)) return FSTAT_ERR_INVALID_ARG;
+  if (n == 0) return FSTAT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = grad_prepare(p, n, st);
+  if (rc) return rc;
   if (p->cand_pending) { CK(cudaEventSynchronize(p->cand_staged)); p->cand_pending = false; }
   if (n > p->ccap) {
     CK(cudaDeviceSynchronize());
@@ -945,21 +972,68 @@ int fstat_grad(fstat_plan* p, const fstat_candidate* cand, int64_t n, float* two
     CK(palloc(p, &p->d_cand, c * sizeof(fstat_candidate)));
     p->ccap = c;
   }
-  const size_t need = grad_scratch_bytes((int)n, p->geo);
-  if (need > p->gscratch_bytes) {
-    CK(cudaDeviceSynchronize());
-    if (p->gscratch) cudaFree(p->gscratch);
-    p->gscratch = nullptr;
-    p->gscratch_bytes = 0;
-    CK(palloc(p, &p->gscratch, need));
-    p->gscratch_bytes = need;
-  }
   std::memcpy(p->h_cand, cand, (size_t)n * sizeof(fstat_candidate));
   CK(cudaMemcpyAsync(p->d_cand, p->h_cand, (size_t)n * sizeof(fstat_candidate), cudaMemcpyHostToDevice, st));
   CK(cudaEventRecord(p->cand_staged, st));
   p->cand_pending = true;
   CK(launch_grad(p->geo, p->gtab, p->d_cand, (int)n, p->gscratch, twoF, grad, st));
   CK(cudaEventRecord(p->done, st));
+  return FSTAT_OK;
+}
+
+int fstat_refine(fstat_plan* p, const fstat_candidate* cand, int64_t n, const double* scales, int steps,
+                 double step0, fstat_candidate* out, float* hist, void* stream) {
+  if (!p || n < 0 || n > INT32_MAX || (n > 0 && (!cand || !out)) || !scales || steps < 0 || steps > 100000 ||
+      !std::isfinite(step0) || !(step0 > 0.0))
+    return FSTAT_ERR_INVALID_ARG;
+  for (int j = 0; j < 4; ++j)
+    if (!std::isfinite(scales[j]) || !(scales[j] > 0.0)) return FSTAT_ERR_INVALID_ARG;
+  for (int X = 0; X < p->d.n_det; ++X)
+    if (!p->have[X]) return FSTAT_ERR_NOT_READY;
+  if (!candidates_finite(cand, n)) return FSTAT_ERR_INVALID_ARG;
+  if (n == 0) return FSTAT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = grad_prepare(p, n, st);
+  if (rc) return rc;
+  // one block: theta, trial | cur, val | g, gt | eta | 2F history
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t nc = up((size_t)n * sizeof(fstat_candidate)), nf = up((size_t)n * sizeof(float));
+  const size_t n4 = up((size_t)n * 4 * sizeof(float)), nd = up((size_t)n * sizeof(double));
+  const size_t nh = up((size_t)(steps + 1) * n * sizeof(float));
+  const size_t need = 2 * nc + 2 * nf + 2 * n4 + nd + nh;
+  if (need > p->rbuf_bytes) {
+    CK(cudaDeviceSynchronize());
+    if (p->rbuf) cudaFree(p->rbuf);
+    p->alloc_bytes -= p->rbuf_bytes;
+    p->rbuf = nullptr;
+    p->rbuf_bytes = 0;
+    CK(palloc(p, &p->rbuf, need));
+    p->rbuf_bytes = need;
+  }
+  char* b = (char*)p->rbuf;
+  AscentState s;
+  s.n = (int)n;
+  s.theta = (fstat_candidate*)b; b += nc;
+  s.trial = (fstat_candidate*)b; b += nc;
+  s.cur = (float*)b; b += nf;
+  s.val = (float*)b; b += nf;
+  s.g = (float*)b; b += n4;
+  s.gt = (float*)b; b += n4;
+  s.eta = (double*)b; b += nd;
+  float* h = (float*)b;
+  CK(cudaMemcpyAsync(s.theta, cand, (size_t)n * sizeof(fstat_candidate), cudaMemcpyHostToDevice, st));
+  CK(launch_grad(p->geo, p->gtab, s.theta, (int)n, p->gscratch, s.cur, s.g, st));
+  CK(launch_ascent_init(s, step0, h, st));
+  for (int k = 0; k < steps; ++k) {
+    CK(launch_ascent_trial(s, scales, st));
+    CK(launch_grad(p->geo, p->gtab, s.trial, (int)n, p->gscratch, s.val, s.gt, st));
+    CK(launch_ascent_accept(s, h + (size_t)(k + 1) * n, st));
+  }
+  // three kernels per evaluation, trial and accept per step, init
+  p->n_launches += 4 + 5 * (int64_t)steps;
+  CK(cudaMemcpyAsync(out, s.theta, (size_t)n * sizeof(fstat_candidate), cudaMemcpyDeviceToHost, st));
+  if (hist) CK(cudaMemcpyAsync(hist, h, (size_t)(steps + 1) * n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return FSTAT_OK;
 }
 

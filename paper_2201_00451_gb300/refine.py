@@ -4,7 +4,8 @@
 evaluates 2F at theta = (f, f1dot, alpha, delta) (float64, one row per
 candidate) with the demodulation sums of eqs. (Fa_DET)/(Fb_DET) of Sec. 2;
 the backward pass multiplies the incoming gradient by the adjoint's
-d2F/dtheta.  ``refine`` runs gradient ascent with per-candidate step control.
+d2F/dtheta.  ``refine`` runs gradient ascent with per-candidate step
+control, the whole loop on the device (fstat_refine).
 """
 
 from __future__ import annotations
@@ -51,24 +52,11 @@ def refine(plan, theta0, scales, steps: int = 20, f2dot=0.0, step0: float = 0.25
     ``scales`` ([4]) are the natural spacings of (f, f1dot, alpha, delta);
     the step moves ``eta`` scaled units along the scaled gradient direction,
     with eta growing by 1.25 on accepted steps and halving on rejected ones
-    (a step that lowers 2F is not taken).  Returns (theta, 2F history [steps+1, n])."""
-    theta = torch.as_tensor(theta0, dtype=torch.float64).clone()
-    s = torch.as_tensor(scales, dtype=torch.float64)
-    n = len(theta)
-    eta = torch.full((n,), step0, dtype=torch.float64)
-    cur, g = plan.grad(_candidates(theta, f2dot))
-    cur, g = cur.double().cpu(), g.double().cpu()
-    hist = [cur.clone()]
-    for _ in range(steps):
-        sg = g * s
-        norm = sg.norm(dim=1).clamp_min(1e-300)
-        trial = theta + (eta / norm)[:, None] * sg * s
-        val, gt = plan.grad(_candidates(trial, f2dot))
-        val, gt = val.double().cpu(), gt.double().cpu()
-        ok = val > cur
-        theta = torch.where(ok[:, None], trial, theta)
-        cur = torch.where(ok, val, cur)
-        g = torch.where(ok[:, None], gt, g)
-        eta = torch.where(ok, eta * 1.25, eta * 0.5)
-        hist.append(cur.clone())
-    return theta, torch.stack(hist)
+    (a step that lowers 2F is not taken).  The loop runs on the device
+    (fstat_refine).  Returns (theta [n, 4] float64, 2F history [steps+1, n]
+    float64)."""
+    theta = torch.as_tensor(theta0, dtype=torch.float64)
+    out, hist = plan.refine(_candidates(theta, f2dot), np.asarray(scales, dtype=np.float64), steps=steps,
+                            step0=step0)
+    th = np.stack([out["f"], out["f1dot"], out["alpha"], out["delta"]], axis=1)
+    return torch.from_numpy(th), torch.from_numpy(hist.astype(np.float64))

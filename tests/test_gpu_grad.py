@@ -111,6 +111,57 @@ def test_refinement_recovers_noise_free_injection():
     plan.close()
 
 
+def _host_ascent(plan, theta, s, steps, step0=0.25):
+    # The ascent rule written out on the host over fstat_grad, each double
+    # operation rounded on its own in the order the rule states it.
+    theta = np.array(theta, dtype=np.float64)
+    eta = np.full(len(theta), step0)
+    cur, g = plan.grad(_cands(theta))
+    cur, g = cur.cpu().numpy(), g.cpu().numpy().astype(np.float64)
+    hist = [cur.copy()]
+    for _ in range(steps):
+        sg = g * s
+        sq = sg * sg
+        nrm = np.sqrt(((sq[:, 0] + sq[:, 1]) + sq[:, 2]) + sq[:, 3])
+        step = eta / np.maximum(nrm, 1e-300)
+        trial = theta + (step[:, None] * sg) * s
+        val, gt = plan.grad(_cands(trial))
+        val, gt = val.cpu().numpy(), gt.cpu().numpy().astype(np.float64)
+        ok = val > cur
+        theta = np.where(ok[:, None], trial, theta)
+        cur = np.where(ok, val, cur)
+        g = np.where(ok[:, None], gt, g)
+        eta = np.where(ok, eta * 1.25, eta * 0.5)
+        hist.append(cur.copy())
+    return theta, np.array(hist)
+
+
+def test_device_ascent_equals_the_host_rule():
+    # fstat_refine (the loop on the device) against the same rule on the
+    # host over fstat_grad: identical candidates and 2F history, bit for bit
+    t, x, plan = _setup(45, rho2=180.0)
+    inj = t.injections[0]
+    s = _scales(t)
+    rng = np.random.default_rng(6)
+    truth = np.array([inj.f0, inj.f1dot, inj.alpha, inj.delta])
+    start = truth + rng.uniform(-0.6, 0.6, (37, 4)) * s
+    th_h, hist_h = _host_ascent(plan, start, s, 12)
+    out, hist_d = plan.refine(_cands(start), s, steps=12)
+    th_d = np.stack([out["f"], out["f1dot"], out["alpha"], out["delta"]], axis=1)
+    assert np.array_equal(hist_d, hist_h.astype(np.float32))
+    assert np.array_equal(th_d, th_h)
+    assert np.all(out["f2dot"] == 0.0)
+    # zero steps: the start and its 2F; bad arguments are refused
+    out0, h0 = plan.refine(_cands(start[:3]), s, steps=0)
+    assert np.array_equal(np.stack([out0["f"], out0["f1dot"], out0["alpha"], out0["delta"]], 1), start[:3])
+    assert np.array_equal(h0[0], hist_h[0][:3].astype(np.float32))
+    for bad_s, bad_steps, bad_eta in ((s * np.array([1, 0, 1, 1]), 3, 0.25), (s, -1, 0.25), (s, 3, 0.0)):
+        with pytest.raises(pkg.FstatError) as e:
+            plan.refine(_cands(start[:3]), bad_s, steps=bad_steps, step0=bad_eta)
+        assert e.value.code == -1
+    plan.close()
+
+
 def test_full_size_refinement_recovers_injections():
     # The 10-day two-detector data (10 injections), 4096 candidates seeded
     # +-0.5 grid step off the injections in (f, f1dot, alpha, delta), 20 ascent
