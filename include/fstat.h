@@ -327,7 +327,7 @@ int fstat_set_split(fstat_plan* plan, int64_t n1);
  * with fstat_compute_peaks) = the first half of the next tile's rows copied
  * into shared memory of their own as soon as the current tile's first pass
  * has read its own, the second half once its last pass has read the
- * buffer.  vb 0..8.  A shape that is not
+ * buffer (fstat_compute_peaks runs schedule 0 in its place).  vb 0..8.  A shape that is not
  * compiled for the current split makes fstat_compute return
  * FSTAT_ERR_CUDA.  fstat_get_cta reports the shapes in effect (a default
  * as its value for the current split). */
