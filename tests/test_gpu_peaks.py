@@ -116,7 +116,9 @@ def test_peaks_equal_dense_for_every_pass_b_schedule():
     for cb, vb in ((4, 0), (4, 2), (4, 4), (4, 6), (2, 2), (8, 6), (4, 8), (8, 8)):
         plan.set_cta(1, cb, 2, vb)
         dense = plan.compute(tm).cpu().numpy()
-        for n_bands in (2, 256, 1 << 13):
+        # whole-row bands of 512, 16 and 8 rows (reduced in registers when a
+        # warp's rows fit one band), 4 rows, and bands inside a row
+        for n_bands in (2, 64, 128, 256, 1 << 13):
             out = plan.compute_peaks(tm, threshold=12.0, n_bands=n_bands, capacity=1 << 18)
             plan.sync()
             blocks = dense.reshape(len(tm), n_bands, -1)
