@@ -170,6 +170,19 @@ __global__ void k_sky_setup(Geo g, double alpha, double delta, SkyConst* out) {
 
 // Cubic Lagrange weights at f = r / kNodeStep between nodes 0 and 1 of
 // nodes at -1, 0, 1, 2 (dyadic f: every weight is exact in FP64).
+// FP32 tap weights: the quotient by the hardware reciprocal (2 ulp; its
+// denominator len sin(pi (d - m)/len) lies between ~pi |d - m| and D + 1),
+// and the Hamming taper's sine and cosine of an angle within +-pi/2 by the
+// hardware unit (~4e-7 absolute on a factor near 1).  The Dirichlet sines
+// themselves keep the accurate sincospi (their arguments can be tiny).  FP64
+// keeps exact division and sincospi throughout.
+__device__ __forceinline__ float tap_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double tap_div(double a, double b) { return a / b; }
+__device__ __forceinline__ void taper_sincospi(float x, float* s, float* c) {
+  __sincosf(3.14159265358979323846f * x, s, c);
+}
+__device__ __forceinline__ void taper_sincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+
 __device__ __forceinline__ void node_weights(int r, double* w) {
   const double f = (double)r * (1.0 / kNodeStep);
   const double fm = f - 1.0, fp = f + 1.0, f2 = f - 2.0;
@@ -390,14 +403,14 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
       T d = (T)dl, sd, cd_, sdl, cdl, sdt = 0, cdt = 0;
       sincospi_t(d, &sd, &cd_);
       sincospi_t(d / len, &sdl, &cdl);
-      if (taper) sincospi_t(d * inv_taper, &sdt, &cdt);
+      if (taper) taper_sincospi(d * inv_taper, &sdt, &cdt);
       for (int m = -D; m <= D; ++m) {
         long long k = k0 + m;
         if (k < 0 || k >= g.n) continue;
         // sin(pi (d - m)) = (-1)^m sin(pi d); sin(pi (d - m)/len) by angle addition
         const T num = (m & 1) ? -sd : sd;
         const T sx = sdl * tab_c[m + D] - cdl * tab_s[m + D];
-        T wgt = num / (len * sx);
+        T wgt = tap_div(num, len * sx);
         if (taper) wgt *= (T)0.54 + (T)0.46 * (cdt * tap_c[m + D] + sdt * tap_s[m + D]);
         TZ v = tap(k);
         zr += (T)v.x * wgt;
