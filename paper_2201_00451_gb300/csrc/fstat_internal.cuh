@@ -96,6 +96,14 @@ struct alignas(32) SkyNode {
   double v;       // (T - t0) / dt - j, T + t_m,X(T) = t_b^j
   double a, b;    // antenna patterns at T
 };
+// The same nodes for the FP32 (mixed-precision) resampling: v = vi + vf with
+// vi = rint(v) exact and |vf| <= 1/2 in FP32, dv = v(next node) - v (small:
+// the delay's change over kNodeStep samples), and a, b in FP32.
+struct alignas(32) NodeF32 {
+  float a, b, vf, dv;
+  int vi;
+  int pad_[3];
+};
 constexpr int kNodeStep = 16;  // samples between timing nodes
 inline int sky_nodes(int64_t n) { return (int)((n + kNodeStep - 1) / kNodeStep) + 3; }
 
@@ -123,7 +131,7 @@ struct Geo {
   // for sample j = (m - 1) kNodeStep: t_m at the detector time, and at the
   // SSB epoch the delay correction v = u - j and the antenna patterns a, b
   SkyNode* nodes;
-  float2* nodes_ab32;                  // (a, b) at the same nodes in FP32 (for G)
+  NodeF32* nodes32;                    // the same nodes in FP32 (mixed path)
   int n_nodes;
 };
 

@@ -67,7 +67,7 @@ struct fstat_plan {
   TimeTab* tab = nullptr;        // timing table (geo.tab)
   double* tm_tab = nullptr;      // per-sky Roemer delay table (geo.tm_tab)
   SkyNode* nodes = nullptr;      // per-sky timing nodes (geo.nodes)
-  float2* nodes_ab32 = nullptr;  // their antenna patterns in FP32 (geo.nodes_ab32)
+  NodeF32* nodes32 = nullptr;  // the same nodes in FP32 (geo.nodes32)
   SkyConst* sky = nullptr;
   void* tw = nullptr;            // twiddle tables for the current split
   TwiddleTables tt{};
@@ -171,7 +171,7 @@ void free_all(fstat_plan* p) {
   if (p->tab) cudaFree(p->tab);
   if (p->tm_tab) cudaFree(p->tm_tab);
   if (p->nodes) cudaFree(p->nodes);
-  if (p->nodes_ab32) cudaFree(p->nodes_ab32);
+  if (p->nodes32) cudaFree(p->nodes32);
   if (p->sky) cudaFree(p->sky);
   if (p->tw) cudaFree(p->tw);
   if (p->d_err) cudaFree(p->d_err);
@@ -404,9 +404,9 @@ int fstat_plan_create(const fstat_plan_desc* desc, fstat_plan** out) {
     g.tm_tab = p->tm_tab;
     g.n_nodes = sky_nodes(N);
     if (e == cudaSuccess) e = palloc(p, &p->nodes, (size_t)g.n_nodes * d.n_det * sizeof(SkyNode));
-    if (e == cudaSuccess) e = palloc(p, &p->nodes_ab32, (size_t)g.n_nodes * d.n_det * sizeof(float2));
+    if (e == cudaSuccess) e = palloc(p, &p->nodes32, (size_t)g.n_nodes * d.n_det * sizeof(NodeF32));
     g.nodes = p->nodes;
-    g.nodes_ab32 = p->nodes_ab32;
+    g.nodes32 = p->nodes32;
     if (e == cudaSuccess) e = launch_time_table(g, tab, 0);
   }
   if (e == cudaSuccess) e = palloc(p, &p->partials, (size_t)3 * p->nblk * sizeof(double));

@@ -9,6 +9,7 @@
 
 #include <math.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "fstat_internal.cuh"
@@ -221,8 +222,27 @@ __global__ void k_sky_nodes(Geo g, const SkyConst* __restrict__ skyp) {
       nd.v = (T_ - g.t0) / g.dt - j;
       antenna(s, X, rot_eval(g, X, T_), &nd.a, &nd.b);
       g.nodes[(int64_t)X * g.n_nodes + m] = nd;
-      g.nodes_ab32[(int64_t)X * g.n_nodes + m] = make_float2((float)nd.a, (float)nd.b);
     }
+  }
+}
+
+// FP32 image of the nodes for the mixed path (NodeF32): the delay split
+// into its exact integer part and an FP32 fraction, and its FP32 change to
+// the next node, formed in FP64 from the FP64 nodes.
+__global__ void k_sky_nodes32(Geo g) {
+  const int64_t total = (int64_t)g.n_det * g.n_nodes;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(i % g.n_nodes);
+    const SkyNode nd = g.nodes[i];
+    NodeF32 f;
+    const double vi = rint(nd.v);
+    f.a = (float)nd.a;
+    f.b = (float)nd.b;
+    f.vi = (int)vi;
+    f.vf = (float)(nd.v - vi);
+    f.dv = m + 1 < g.n_nodes ? (float)(g.nodes[i + 1].v - nd.v) : 0.f;
+    f.pad_[0] = f.pad_[1] = f.pad_[2] = 0;
+    g.nodes32[i] = f;
   }
 }
 
@@ -340,9 +360,26 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
     // the antenna patterns at T, interpolated between the timing nodes
     const int64_t node0 = (int64_t)X * g.n_nodes + (min(j, j_last) / kNodeStep + 1);
     const SkyNode* nd = g.nodes + node0;
-    double u = (double)j + (wn[0] * nd[-1].v + wn[1] * nd[0].v + wn[2] * nd[1].v + wn[3] * nd[2].v);
-    if constexpr (kNegCtrlFp32) u = (double)((float)j + (float)(u - (double)j));
-    const long long k0 = __double2ll_rn(u);
+    // k0 = rint(u) and dlt = u - k0 for u = j + v.  FP32 path: v = vi + vf
+    // at this segment's node, plus the weighted node-to-node changes (the
+    // interpolating cubic written about that node), so the integer part is
+    // exact and only the fraction, |f| <~ 1/2, is rounded to FP32.  FP64
+    // plans (and the FP32-timing negative control) form u in FP64.
+    long long k0;
+    T dlt;
+    if constexpr (sizeof(T) == sizeof(float) && !kNegCtrlFp32) {
+      const NodeF32* nf = g.nodes32 + node0;
+      const float dv0 = nf[0].dv;
+      const float f = nf[0].vf + ((wf[2] * dv0 + wf[3] * (dv0 + nf[1].dv)) - wf[0] * nf[-1].dv);
+      const float rf = rintf(f);
+      k0 = j + nf[0].vi + (long long)rf;
+      dlt = f - rf;
+    } else {
+      double u = (double)j + (wn[0] * nd[-1].v + wn[1] * nd[0].v + wn[2] * nd[1].v + wn[3] * nd[2].v);
+      if constexpr (kNegCtrlFp32) u = (double)((float)j + (float)(u - (double)j));
+      k0 = __double2ll_rn(u);
+      dlt = (T)(u - (double)k0);
+    }
     // the block's window of detector samples (u is monotonic in j)
     __syncthreads();  // the previous detector's window has been read
     if (j == j0) s_span[0] = k0;
@@ -389,18 +426,18 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
       sab += w * a * b;
     }
     if (!valid) continue;
-    double dl = u - (double)k0;
+
     auto tap = [&](long long k) -> TZ {
       const long long i = k - lo;
       return (i >= 0 && i < kWin) ? win[i] : zx[k];
     };
     T zr = 0, zi = 0;
-    if (dl == 0.0) {
+    if (dlt == (T)0) {
       TZ v = tap(k0);
       zr = (T)v.x;
       zi = (T)v.y;
     } else {
-      T d = (T)dl, sd, cd_, sdl, cdl, sdt = 0, cdt = 0;
+      T d = dlt, sd, cd_, sdl, cdl, sdt = 0, cdt = 0;
       sincospi_t(d, &sd, &cd_);
       sincospi_t(d / len, &sdl, &cdl);
       if (taper) taper_sincospi(d * inv_taper, &sdt, &cdt);
@@ -420,9 +457,9 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
     // the antenna-weighted detector sum G (FP32 a, b in the mixed path)
     T wa, wb;
     if constexpr (sizeof(T) == sizeof(float)) {
-      const float2* ab = g.nodes_ab32 + node0;
-      const float a = wf[0] * ab[-1].x + wf[1] * ab[0].x + wf[2] * ab[1].x + wf[3] * ab[2].x;
-      const float b = wf[0] * ab[-1].y + wf[1] * ab[0].y + wf[2] * ab[1].y + wf[3] * ab[2].y;
+      const NodeF32* ab = g.nodes32 + node0;
+      const float a = wf[0] * ab[-1].a + wf[1] * ab[0].a + wf[2] * ab[1].a + wf[3] * ab[2].a;
+      const float b = wf[0] * ab[-1].b + wf[1] * ab[0].b + wf[2] * ab[1].b + wf[3] * ab[2].b;
       const float wx = (float)w;
       wa = wx * a;
       wb = wx * b;
@@ -571,6 +608,10 @@ void launch_sky(const Geo& g, int precision, double alpha, double delta, const v
   k_sky_setup<<<1, 32, 0, st>>>(g, alpha, delta, sky);
   k_sky_table<<<(g.tab_n + 255) / 256, 256, 0, st>>>(g, sky);
   k_sky_nodes<<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, sky);
+  if (precision != FSTAT_FP64) {
+    const int64_t total = (int64_t)g.n_det * g.n_nodes;
+    k_sky_nodes32<<<(int)std::min<int64_t>((total + 255) / 256, 8 * device_sm_count()), 256, 0, st>>>(g);
+  }
   for (int X = 0; X < g.n_det; ++X) {
     bool in64 = xh_dtype[X] == FSTAT_C128;
     if (precision == FSTAT_FP64) {
