@@ -96,13 +96,16 @@ struct alignas(32) SkyNode {
   double v;       // (T - t0) / dt - j, T + t_m,X(T) = t_b^j
   double a, b;    // antenna patterns at T
 };
-// The same nodes for the FP32 (mixed-precision) resampling: v = vi + vf with
+// The same nodes for the FP32 (mixed-precision) path: v = vi + vf with
 // vi = rint(v) exact and |vf| <= 1/2 in FP32, dv = v(next node) - v (small:
-// the delay's change over kNodeStep samples), and a, b in FP32.
+// the delay's change over kNodeStep samples), a, b in FP32; and the step-iii
+// phase f_h t_m at the detector-time node as its fraction phf (|phf| <= 1/2)
+// and its change to the next node dph (below a cycle), both formed in FP64.
 struct alignas(32) NodeF32 {
   float a, b, vf, dv;
   int vi;
-  int pad_[3];
+  float phf, dph;
+  int pad_;
 };
 constexpr int kNodeStep = 16;  // samples between timing nodes
 inline int sky_nodes(int64_t n) { return (int)((n + kNodeStep - 1) / kNodeStep) + 3; }

@@ -234,14 +234,18 @@ __global__ void k_sky_nodes32(Geo g) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int m = (int)(i % g.n_nodes);
     const SkyNode nd = g.nodes[i];
+    const bool next = m + 1 < g.n_nodes;
     NodeF32 f;
     const double vi = rint(nd.v);
     f.a = (float)nd.a;
     f.b = (float)nd.b;
     f.vi = (int)vi;
     f.vf = (float)(nd.v - vi);
-    f.dv = m + 1 < g.n_nodes ? (float)(g.nodes[i + 1].v - nd.v) : 0.f;
-    f.pad_[0] = f.pad_[1] = f.pad_[2] = 0;
+    f.dv = next ? (float)(g.nodes[i + 1].v - nd.v) : 0.f;
+    const double ph = g.f_het * nd.tm_det;
+    f.phf = (float)(ph - rint(ph));
+    f.dph = next ? (float)(g.f_het * (g.nodes[i + 1].tm_det - nd.tm_det)) : 0.f;
+    f.pad_ = 0;
     g.nodes32[i] = f;
   }
 }
@@ -255,20 +259,53 @@ __global__ void k_sky_nodes32(Geo g) {
 template <typename TIn, typename TZ>
 __global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* __restrict__ z) {
   __shared__ double s_w[kNodeStep][4];  // the node weights, by sample mod kNodeStep
-  if (threadIdx.x < kNodeStep) node_weights(threadIdx.x, s_w[threadIdx.x]);
+  __shared__ float s_wf[kNodeStep][4];
+  if (threadIdx.x < kNodeStep) {
+    node_weights(threadIdx.x, s_w[threadIdx.x]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s_wf[threadIdx.x][q] = (float)s_w[threadIdx.x][q];
+  }
   __syncthreads();
+  // FP32 path: the phase's fraction from the FP32 node image (the cubic
+  // written about the segment's node, |result| <~ 1/2 before the final
+  // reduction); FP64 plans and the negative control form f_h t_m in FP64
+  constexpr bool kSplit = sizeof(TZ) == sizeof(float2) && !kNegCtrlFp32;
   const SkyNode* nd = g.nodes + (int64_t)X * g.n_nodes;
+  const NodeF32* nf32 = g.nodes32 + (int64_t)X * g.n_nodes;
+  const float isf = (float)g.inv_sigma_ref;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < g.n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t m = k / kNodeStep + 1;
-    const double* w = s_w[k % kNodeStep];
-    const double tm = w[0] * nd[m - 1].tm_det + w[1] * nd[m].tm_det + w[2] * nd[m + 1].tm_det + w[3] * nd[m + 2].tm_det;
-    double ph = g.f_het * tm;
-    if constexpr (kNegCtrlFp32) ph = (double)((float)g.f_het * (float)tm);
-    ph -= floor(ph);
+    double ph = 0.0;  // FP64 path: the phase in cycles, in [0, 1)
+    float phs = 0.f;  // FP32 path: the same, in [-1/2, 1/2]
+    if constexpr (kSplit) {
+      const float* wf = s_wf[k % kNodeStep];
+      const NodeF32* nf = nf32 + m;
+      const float d0 = nf[0].dph;
+      const float p = nf[0].phf + ((wf[2] * d0 + wf[3] * (d0 + nf[1].dph)) - wf[0] * nf[-1].dph);
+      phs = p - rintf(p);
+    } else {
+      const double* w = s_w[k % kNodeStep];
+      const double tm = w[0] * nd[m - 1].tm_det + w[1] * nd[m].tm_det + w[2] * nd[m + 1].tm_det + w[3] * nd[m + 2].tm_det;
+      ph = g.f_het * tm;
+      if constexpr (kNegCtrlFp32) ph = (double)((float)g.f_het * (float)tm);
+      ph -= floor(ph);
+    }
     TIn x = xh[k];
     const double is = g.inv_sigma_ref;
-    if constexpr (sizeof(TZ) == sizeof(float2)) {
+    if constexpr (kSplit) {
+      float sn, cs;
+      sincospif(2.0f * phs, &sn, &cs);
+      float xr, xi;
+      if constexpr (sizeof(TIn) == sizeof(float2)) {
+        xr = x.x * isf;
+        xi = x.y * isf;
+      } else {
+        xr = (float)((double)x.x * is);
+        xi = (float)((double)x.y * is);
+      }
+      z[k] = make_float2(xr * cs + xi * sn, xi * cs - xr * sn);
+    } else if constexpr (sizeof(TZ) == sizeof(float2)) {
       float sn, cs;
       sincospif(2.0f * (float)ph, &sn, &cs);
       float xr = (float)((double)x.x * is), xi = (float)((double)x.y * is);
@@ -293,9 +330,10 @@ __global__ void k_detector_phase(Geo g, int X, const TIn* __restrict__ xh, TZ* _
 // cos, sin(pi m / (D + 1)), m = -D..D: two sine/cosine evaluations per
 // sample instead of two per tap.
 //
-// FP64 work per sample is kept to what needs it: u (the sample position,
-// from the nodes' v) in FP64; a, b for the weighted sum G in FP32 from FP32
-// copies of the node values (G itself is FP32; the FP64 path keeps FP64);
+// FP64 work per sample is kept to what needs it: the sample position u and
+// a, b for the weighted sum G come from the FP32 image of the nodes in the
+// mixed path (u's integer part exact, its fraction to ~6e-8 samples; G
+// itself is FP32; the FP64 path keeps FP64 throughout);
 // and A, B, C per 16-sample segment: with a(r) = sum_q W_rq a_q the cubic
 // interpolant of the segment's four node values a_q, the segment's
 // sum_r a(r)^2 is the quadratic form a^T M a with M = sum_r W_r W_r^T
