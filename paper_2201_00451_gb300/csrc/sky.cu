@@ -378,6 +378,8 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
 #pragma unroll
     for (int q = 0; q < 4; ++q) s_wf[threadIdx.x][q] = (float)s_w[threadIdx.x][q];
   }
+  __shared__ float s_wx[kMaxDet];  // noise weights in FP32 (the mixed path's G)
+  if (threadIdx.x < g.n_det) s_wx[threadIdx.x] = (float)g.w[threadIdx.x];
   __syncthreads();
   if (threadIdx.x < 16) {
     const int q = threadIdx.x >> 2, r2 = threadIdx.x & 3;
@@ -392,6 +394,7 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
   const float* wf = s_wf[j % kNodeStep];
   const unsigned lane = threadIdx.x & 31;
   double sa = 0.0, sb = 0.0, sab = 0.0;
+  bool summed = false;  // this thread added to sa, sb, sab
   Pair<T> acc = pzero<T>();
   for (int X = 0; X < g.n_det; ++X) {
     // steps (iv)-(v): the sample position u of T (T + t_m(T) = t_b^j) and
@@ -459,6 +462,7 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
     if (!seg_full && valid) {
       const double a = wn[0] * nd[-1].a + wn[1] * nd[0].a + wn[2] * nd[1].a + wn[3] * nd[2].a;
       const double b = wn[0] * nd[-1].b + wn[1] * nd[0].b + wn[2] * nd[1].b + wn[3] * nd[2].b;
+      summed = true;
       sa += w * a * a;
       sb += w * b * b;
       sab += w * a * b;
@@ -498,7 +502,7 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
       const NodeF32* ab = g.nodes32 + node0;
       const float a = wf[0] * ab[-1].a + wf[1] * ab[0].a + wf[2] * ab[1].a + wf[3] * ab[2].a;
       const float b = wf[0] * ab[-1].b + wf[1] * ab[0].b + wf[2] * ab[1].b + wf[3] * ab[2].b;
-      const float wx = (float)w;
+      const float wx = s_wx[X];
       wa = wx * a;
       wb = wx * b;
     } else {
@@ -541,17 +545,23 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
         aMb += av[q] * mb;
       }
       const double w = g.w[X];
+      summed = true;
       sa += w * aMa;
       sb += w * bMb;
       sab += w * aMb;
     }
   }
-  // block reduction of the A, B, C partial sums (fixed order)
+  // block reduction of the A, B, C partial sums (fixed order).  Only the
+  // warps that summed anything reduce (the segment sums sit in the first
+  // n_det kSeg threads, per-sample sums arise only at the data's edges):
+  // the others' zeros would not change a bit of the result.
   __shared__ double red[3][kSkyBlock / 32];
-  for (int o = 16; o > 0; o >>= 1) {
-    sa += __shfl_down_sync(0xffffffffu, sa, o);
-    sb += __shfl_down_sync(0xffffffffu, sb, o);
-    sab += __shfl_down_sync(0xffffffffu, sab, o);
+  if (__any_sync(0xffffffffu, summed)) {
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_down_sync(0xffffffffu, sa, o);
+      sb += __shfl_down_sync(0xffffffffu, sb, o);
+      sab += __shfl_down_sync(0xffffffffu, sab, o);
+    }
   }
   const int wid = threadIdx.x >> 5;
   if (lane == 0) { red[0][wid] = sa; red[1][wid] = sb; red[2][wid] = sab; }
