@@ -184,6 +184,13 @@ __device__ __forceinline__ void taper_sincospi(float x, float* s, float* c) {
 }
 __device__ __forceinline__ void taper_sincospi(double x, double* s, double* c) { sincospi(x, s, c); }
 
+// Per-tap constants of the interpolation kernel, one aligned entry per tap
+// m = -D..D: cos, sin(pi m / len) (the Dirichlet denominator by angle
+// addition) and cos, sin(pi m / (D + 1)) (the taper).
+template <typename T> struct alignas(4 * sizeof(T)) TapK {
+  T c, s, tc, ts;
+};
+
 __device__ __forceinline__ void node_weights(int r, double* w) {
   const double f = (double)r * (1.0 / kNodeStep);
   const double fm = f - 1.0, fp = f + 1.0, f2 = f - 2.0;
@@ -350,7 +357,7 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
            typename PairMem<T>::type* __restrict__ G, int n1, int64_t lc, double* __restrict__ partials) {
   (void)skyp;  // the sky position enters through the timing nodes
   __shared__ __align__(16) TZ win[kWin];
-  __shared__ T tab_c[2 * kMaxD + 1], tab_s[2 * kMaxD + 1], tap_c[2 * kMaxD + 1], tap_s[2 * kMaxD + 1];
+  __shared__ TapK<T> tk[2 * kMaxD + 1];
   __shared__ long long s_span[2];
   __shared__ double s_w[kNodeStep][4], s_m[4][4];  // node weights by j mod kNodeStep; segment matrix M
   __shared__ float s_wf[kNodeStep][4];
@@ -366,12 +373,14 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
   const T inv_taper = (T)1 / (T)(D + 1);
   for (int m = threadIdx.x; m <= 2 * D; m += blockDim.x) {
     T sn, cs;
+    TapK<T> q;
     sincospi_t((T)(m - D) / len, &sn, &cs);
-    tab_c[m] = cs;
-    tab_s[m] = sn;
+    q.c = cs;
+    q.s = sn;
     sincospi_t((T)(m - D) * inv_taper, &sn, &cs);
-    tap_c[m] = cs;
-    tap_s[m] = sn;
+    q.tc = cs;
+    q.ts = sn;
+    tk[m] = q;
   }
   if (threadIdx.x < kNodeStep) {
     node_weights(threadIdx.x, s_w[threadIdx.x]);
@@ -483,17 +492,35 @@ k_resample(Geo g, const SkyConst* __restrict__ skyp, const TZ* __restrict__ z,
       sincospi_t(d, &sd, &cd_);
       sincospi_t(d / len, &sdl, &cdl);
       if (taper) taper_sincospi(d * inv_taper, &sdt, &cdt);
-      for (int m = -D; m <= D; ++m) {
-        long long k = k0 + m;
-        if (k < 0 || k >= g.n) continue;
+      auto weight = [&](int m) -> T {
         // sin(pi (d - m)) = (-1)^m sin(pi d); sin(pi (d - m)/len) by angle addition
+        const TapK<T> q = tk[m + D];
         const T num = (m & 1) ? -sd : sd;
-        const T sx = sdl * tab_c[m + D] - cdl * tab_s[m + D];
+        const T sx = sdl * q.c - cdl * q.s;
         T wgt = tap_div(num, len * sx);
-        if (taper) wgt *= (T)0.54 + (T)0.46 * (cdt * tap_c[m + D] + sdt * tap_s[m + D]);
-        TZ v = tap(k);
-        zr += (T)v.x * wgt;
-        zi += (T)v.y * wgt;
+        if (taper) wgt *= (T)0.54 + (T)0.46 * (cdt * q.tc + sdt * q.ts);
+        return wgt;
+      };
+      const long long i0 = k0 - D - lo;  // window index of tap -D
+      if (k0 - D >= 0 && k0 + D < g.n && i0 >= 0 && i0 + 2 * D < kWin) {
+        // every tap inside the data and the staged window (the usual case):
+        // the same sum without per-tap checks
+        const TZ* wp = win + i0;
+        for (int m = -D; m <= D; ++m) {
+          const T wgt = weight(m);
+          const TZ v = wp[m + D];
+          zr += (T)v.x * wgt;
+          zi += (T)v.y * wgt;
+        }
+      } else {
+        for (int m = -D; m <= D; ++m) {
+          const long long k = k0 + m;
+          if (k < 0 || k >= g.n) continue;
+          const T wgt = weight(m);
+          const TZ v = tap(k);
+          zr += (T)v.x * wgt;
+          zi += (T)v.y * wgt;
+        }
       }
     }
     // the antenna-weighted detector sum G (FP32 a, b in the mixed path)
