@@ -1023,6 +1023,7 @@ def e2e_peaks(t, xs, tm, chunk, dev, stream, args, steps):
     torch.cuda.synchronize(dev)
     dev_s = e0.elapsed_time(e1) * 1e-3
     n_cross = int(hcount.sum())
+    peaks_shape = list(plan.peaks_cta)
     plan.close()
     n = len(tm) * steps
     return {"value": n / el, "unit": UNIT,
@@ -1030,7 +1031,7 @@ def e2e_peaks(t, xs, tm, chunk, dev, stream, args, steps):
             "d2h_bytes_per_step": int(hmax.nbytes + hbin.nbytes + hcount.nbytes + hpeaks.nbytes),
             "output": f"{PEAK_BANDS} band maxima (2F, bin) per template + list of 2F > {PEAK_THRESHOLD:g}",
             "crossings_per_step": n_cross,
-            "device_value": n / dev_s}
+            "device_value": n / dev_s, "pass_b_shape": peaks_shape}
 
 
 def main():

@@ -380,11 +380,20 @@ int fstat_set_wait_limit(fstat_plan* plan, int polls);
 
 /* Autotuner: times every compiled (split, ca, va, cb, vb) for this plan's n_fft on
  * the current data with CUDA events on `stream` and keeps the fastest.
+ * Then, at that split, it times pass B of fstat_compute_peaks on its own
+ * (256 whole-row bands, threshold 70) over every compiled (cb, vb) and keeps
+ * the fastest for that mode (without the 2F store its best shape can
+ * differ).  fstat_set_cta makes both modes use the shape it sets.
  * Results are cached per (GPU name, n_samples, n_fft, precision, n_det) in
  * the process and, if the environment variable FSTAT_AUTOTUNE_CACHE names
  * a file, in that file.  Synchronises; invalidates cached per-sky work.
  * Errors: NOT_READY (no data), OOM, CUDA. */
 int fstat_autotune(fstat_plan* plan, void* stream);
+
+/* The pass-B shape fstat_compute_peaks runs with (the autotuner's choice
+ * for that mode, else the shape of fstat_get_cta), default resolved.
+ * Errors: INVALID_ARG. */
+int fstat_get_peaks_cta(const fstat_plan* plan, int* cb, int* vb);
 
 /* 2F for one template from a caller-supplied resampled series, allocating
  * nothing.  The paper has no counterpart: this exists for callers that may

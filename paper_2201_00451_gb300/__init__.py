@@ -49,7 +49,7 @@ EXPORTS = (
     "fstat_compute_peaks", "fstat_semicoherent", "fstat_set_residency", "fstat_get_residency",
     "fstat_set_sfts", "fstat_export_data", "fstat_reduce_peaks", "fstat_set_wait_limit",
     "fstat_probe_fma", "fstat_launch_count", "fstat_set_fused", "fstat_get_fused", "fstat_probe_dft16",
-    "fstat_refine",
+    "fstat_refine", "fstat_get_peaks_cta",
 )
 
 
@@ -140,6 +140,7 @@ def open_library(path: str) -> ctypes.CDLL:
         "fstat_strerror": (ctypes.c_char_p, [i32]),
         "fstat_twoF_noalloc": (i32, [P, i64, i64, dbl, dbl, dbl, dbl, dbl, dbl, dbl, P, P]),
         "fstat_get_cta": (i32, [P] + [ctypes.POINTER(i32)] * 4),
+        "fstat_get_peaks_cta": (i32, [P] + [ctypes.POINTER(i32)] * 2),
         "fstat_set_cta": (i32, [P, i32, i32, i32, i32]),
         "fstat_autotune": (i32, [P, P]),
         "fstat_grad": (i32, [P, P, i64, P, P, P]),
@@ -466,6 +467,13 @@ class FstatPlan:
         """(ca, va, cb, vb): pass-A columns/CTA and radix schedule, pass-B rows/CTA and schedule."""
         v = [ctypes.c_int() for _ in range(4)]
         _check(self._lib.fstat_get_cta(self._p, *[ctypes.byref(x) for x in v]), "fstat_get_cta")
+        return tuple(x.value for x in v)
+
+    @property
+    def peaks_cta(self):
+        """(cb, vb): the pass-B shape of compute_peaks (tuned apart by autotune)."""
+        v = [ctypes.c_int() for _ in range(2)]
+        _check(self._lib.fstat_get_peaks_cta(self._p, *[ctypes.byref(x) for x in v]), "fstat_get_peaks_cta")
         return tuple(x.value for x in v)
 
     @property

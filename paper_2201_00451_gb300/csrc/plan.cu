@@ -72,6 +72,7 @@ struct fstat_plan {
   void* tw = nullptr;            // twiddle tables for the current split
   TwiddleTables tt{};
   int ca = 0, cb = 0;            // CTA shapes of pass A / pass B (0 = default)
+  int cb_pk = -1, vb_pk = -1;    // pass B of the peaks mode when tuned apart (-1: cb, vb)
   int va = 0, vb = 0;            // schedules of pass A / pass B (bit 0 radix-8 first, bit 1 one buffer,
                                  // bit 2 pass B tile loads by TMA, bit 3 pass A three CTAs per SM)
   int ra = 0, rb = 0;            // persistent CTAs per SM of pass A / pass B (0 = all resident)
@@ -673,7 +674,8 @@ int enqueue_compute(fstat_plan* p, const fstat_template* h_tmpl, const int* h_or
         cudaEventRecord(ea.b, s); p->ev[0].push_back(ea); p->launches[0]++;
         eb = get_events(p); cudaEventRecord(eb.a, s);
       }
-      e = launch_b(p, p->cb, p->vb, out, s, Zb, po ? &pk : nullptr);
+      const bool own = po && p->cb_pk >= 0;  // the peaks mode's own pass-B shape
+      e = launch_b(p, own ? p->cb_pk : p->cb, own ? p->vb_pk : p->vb, out, s, Zb, po ? &pk : nullptr);
       if (e != cudaSuccess) return cuda_status(e);
       if (prof) { cudaEventRecord(eb.b, s); p->ev[1].push_back(eb); p->launches[1]++; }
     }
@@ -1157,6 +1159,14 @@ int fstat_get_cta(const fstat_plan* p, int* ca, int* va, int* cb, int* vb) {
   return FSTAT_OK;
 }
 
+int fstat_get_peaks_cta(const fstat_plan* p, int* cb, int* vb) {
+  if (!p || !cb || !vb) return FSTAT_ERR_INVALID_ARG;
+  const int c = p->cb_pk >= 0 ? p->cb_pk : p->cb;
+  *cb = c > 0 ? c : fft_default_c(p->log2n1, 1, p->d.precision);
+  *vb = p->cb_pk >= 0 ? p->vb_pk : p->vb;
+  return FSTAT_OK;
+}
+
 int fstat_set_residency(fstat_plan* p, int ra, int rb) {
   if (!p || ra < 0 || rb < 0 || ra > 32 || rb > 32) return FSTAT_ERR_INVALID_ARG;
   p->ra = ra;
@@ -1204,6 +1214,7 @@ int fstat_set_cta(fstat_plan* p, int ca, int va, int cb, int vb) {
   p->va = va;
   p->cb = cb;
   p->vb = vb;
+  p->cb_pk = p->vb_pk = -1;  // the peaks mode follows the set shape
   return FSTAT_OK;
 }
 
@@ -1214,6 +1225,7 @@ namespace {
 
 struct Choice {
   int l1, ca, va, cb, vb, fused;
+  int cbp = -1, vbp = -1;  // pass B of the peaks mode
 };
 std::mutex g_tune_mu;
 std::map<std::string, Choice> g_tune_cache;
@@ -1223,7 +1235,7 @@ std::string tune_key(const fstat_plan* p) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) prop.name[0] = 0;
   char buf[400];
-  std::snprintf(buf, sizeof buf, "v4|%s|N=%lld|nfft=%lld|prec=%d|ndet=%d|ns=%d", prop.name,
+  std::snprintf(buf, sizeof buf, "v5|%s|N=%lld|nfft=%lld|prec=%d|ndet=%d|ns=%d", prop.name,
                 (long long)p->d.n_samples, (long long)p->d.n_fft, p->d.precision, p->d.n_det, p->nstream);
   for (char* c = buf; *c; ++c)
     if (*c == ' ' || *c == '\t') *c = '_';
@@ -1238,7 +1250,7 @@ void load_tune_file() {
   std::ifstream in(f);
   std::string key;
   Choice c;
-  while (in >> key >> c.l1 >> c.ca >> c.va >> c.cb >> c.vb >> c.fused) g_tune_cache[key] = c;
+  while (in >> key >> c.l1 >> c.ca >> c.va >> c.cb >> c.vb >> c.fused >> c.cbp >> c.vbp) g_tune_cache[key] = c;
 }
 
 void save_tune(const std::string& key, const Choice& c) {
@@ -1246,7 +1258,8 @@ void save_tune(const std::string& key, const Choice& c) {
   const char* f = std::getenv("FSTAT_AUTOTUNE_CACHE");
   if (!f) return;
   std::ofstream out(f, std::ios::app);
-  out << key << " " << c.l1 << " " << c.ca << " " << c.va << " " << c.cb << " " << c.vb << " " << c.fused << "\n";
+  out << key << " " << c.l1 << " " << c.ca << " " << c.va << " " << c.cb << " " << c.vb << " " << c.fused << " "
+      << c.cbp << " " << c.vbp << "\n";
 }
 
 // mean time (ms) of `reps` launches of pass A (which = 0) or pass B (which = 1)
@@ -1270,6 +1283,44 @@ float time_pass(fstat_plan* p, int which, int c, int v, const TmplCoef* coef, fl
   return ms / reps;
 }
 
+// Pass B of the peaks mode alone over every compiled shape at the current
+// split: 256 whole-row bands and the threshold 70 of Sec. 5.4 (no 2F store,
+// so its best shape can differ from the dense pass's).  Returns the fastest
+// (cb, vb), or (-1, -1) when none ran.
+void tune_peaks(fstat_plan* p, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int* cbp, int* vbp) {
+  *cbp = *vbp = -1;
+  if (p->d.n_fft < 256) return;
+  unsigned long long* keys = nullptr;
+  fstat_peak* list = nullptr;
+  if (cudaMalloc(&keys, (256 + 1) * sizeof(unsigned long long)) != cudaSuccess) return;
+  if (cudaMalloc(&list, 1024 * sizeof(fstat_peak)) != cudaSuccess) { cudaFree(keys); return; }
+  PeakArgs pk{};
+  pk.band_key = keys;
+  pk.count = keys + 256;
+  pk.peaks = list;
+  pk.cap = 1024;
+  pk.thr = 70.f;
+  pk.log2_band = ilog2_exact(p->d.n_fft) - 8;
+  static const int kCb[] = {0, 1, 2, 4, 8};
+  float best = 1e30f;
+  for (int v = 0; v < 8; ++v) {
+    for (int c : kCb) {
+      cudaMemsetAsync(keys, 0, (256 + 1) * sizeof(unsigned long long), st);
+      if (launch_b(p, c, v, nullptr, st, nullptr, &pk) != cudaSuccess) { cudaGetLastError(); continue; }
+      const int reps = 5;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps; ++r) launch_b(p, c, v, nullptr, st, nullptr, &pk);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / reps < best) { best = ms / reps; *cbp = c; *vbp = v; }
+    }
+  }
+  cudaFree(keys);
+  cudaFree(list);
+}
+
 }  // namespace
 
 extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
@@ -1291,6 +1342,8 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
       p->cb = it->second.cb;
       p->vb = it->second.vb;
       p->fused = it->second.fused != 0 && fused_ok(p);
+      p->cb_pk = it->second.cbp;
+      p->vb_pk = it->second.vbp;
       return FSTAT_OK;
     }
   }
@@ -1402,18 +1455,22 @@ extern "C" int fstat_autotune(fstat_plan* p, void* stream) {
       p->fused = false;
     }
   }
+  cudaFree(out);
+  if (rc == FSTAT_OK) rc = set_split(p, best.l1);
+  if (rc == FSTAT_OK) {
+    p->ca = best.ca;
+    p->va = best.va;
+    p->cb = best.cb;
+    p->vb = best.vb;
+    p->fused = best.fused != 0 && fused_ok(p);
+    tune_peaks(p, st, e0, e1, &best.cbp, &best.vbp);
+    p->cb_pk = best.cbp;
+    p->vb_pk = best.vbp;
+  }
   p->prof = saved_prof;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFree(out);
   if (rc) return rc;
-  rc = set_split(p, best.l1);
-  if (rc) return rc;
-  p->ca = best.ca;
-  p->va = best.va;
-  p->cb = best.cb;
-  p->vb = best.vb;
-  p->fused = best.fused != 0 && fused_ok(p);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   save_tune(key, best);
   return FSTAT_OK;

@@ -132,6 +132,26 @@ def test_peaks_equal_dense_for_every_pass_b_schedule():
     plan.close()
 
 
+def test_autotuned_peaks_shape_equals_dense():
+    # the autotuner picks pass B of the peaks mode apart from the dense
+    # pass; its reduction still equals the dense output's, and an explicit
+    # shape applies to both modes again
+    t, x, plan = setup(58, n_fft=1 << 20, n=400_003)
+    tm = t.templates()
+    plan.autotune()
+    dense = plan.compute(tm).cpu().numpy()
+    cb, vb = plan.peaks_cta
+    assert cb > 0 and 0 <= vb <= 7
+    out = plan.compute_peaks(tm, threshold=12.0, n_bands=256, capacity=1 << 18)
+    plan.sync()
+    blocks = dense.reshape(len(tm), 256, -1)
+    assert np.array_equal(out["band_max"].cpu().numpy(), blocks.max(axis=2))
+    assert np.array_equal(out["band_bin"].cpu().numpy(), blocks.argmax(axis=2) + blocks.shape[2] * np.arange(256))
+    plan.set_cta(1, 4, 2, 6)
+    assert plan.peaks_cta == (4, 6)
+    plan.close()
+
+
 def test_capacity_overflow_and_appending_calls():
     t, x, plan = setup(53)
     tm = t.templates()
